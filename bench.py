@@ -1,0 +1,386 @@
+"""Benchmark of the axisymmetric phase-field MRT-LB step on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+                [--workload batched|oscillating|static] [--precision mix_fp16|fp32|...]
+
+Default workload: the batched case set (512 independent static and
+oscillating droplet cases, grids drawn from seed 20181022 between 64 x 128 and
+256 x 512, density ratios 10/100/1000) advancing together, one kernel launch
+per time step, 16-bit deviation-stored populations with FP32 arithmetic.
+Per-step inputs (~2.5-4.5 GB of populations) are far larger than L2 (129 MB),
+so no flush is needed between steps.  The same JSON line also reports the
+plain FP32 single-case path on the 128 x 256 oscillating drop (L2 flushed
+between timed steps) and the FP64 path.
+
+One step = one pass of the whole hot path over every case: phi recovery,
+stencils, macroscopic recovery, both MRT collisions, streaming with the
+boundary rules.  MLUPS = lattice nodes x steps / seconds / 1e6.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % HBM roofline: FP64/FP32 vs mixed-precision/batched at stated error"
+# Algorithmic bytes per node update (populations read + written, f_0 ledger in
+# FP64, chi^{n-1} read + written; the lagged-p array is not touched).
+BYTES_PER_NODE = {
+    "fp64": 2 * (9 * 8 + 9 * 8 + 2 * 8),       # 320
+    "fp32": 2 * (8 + 8 * 4 + 9 * 4 + 2 * 4),    # 168
+    "mix_fp16": 2 * (8 + 8 * 2 + 9 * 2 + 2 * 4),  # 100
+    "mix_bf16": 2 * (8 + 8 * 2 + 9 * 2 + 2 * 4),  # 100
+}
+DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf16": "f32 (bf16 storage)"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return float(d.get("hbm_gbs")), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_cases(workload: str, precision: str, rank: int, ncases: int = 512):
+    from paper_1810_09299_gb300 import workloads as W
+    if workload == "batched":
+        cases = W.batched_cases(ncases, seed=20181022 + rank, precision=precision)
+    elif workload == "oscillating":
+        cases = [dict(W.oscillating_drop(), precision=precision)]
+    elif workload == "static":
+        cases = [dict(W.static_drop(), precision=precision)]
+    else:
+        raise ValueError(workload)
+    return cases
+
+
+def time_steps(sim, torch, steps: int, flush=None):
+    """Per-step CUDA-event timing on the handle's (torch's current) stream."""
+    st = torch.cuda.current_stream()
+    times = []
+    if flush is None:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(st)
+        for i in range(steps):
+            sim.step(1)
+            ev[i + 1].record(st)
+        torch.cuda.synchronize()
+        times = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+        return times
+    for i in range(steps):
+        flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        sim.step(1)
+        b.record(st)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    return times
+
+
+def cpu_baseline(case: dict, budget_s: float = 15.0):
+    """The FP64 oracle (as it stands) on the host cores, on one case of the
+    workload for a bounded number of steps."""
+    import oracle
+    from paper_1810_09299_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    c = dict(case, precision="fp64")
+    o = oracle.Oracle(c).init(W.initial_phi(c))
+    nodes = c["nr"] * c["nz"]
+    t0 = time.perf_counter()
+    o.step(2)
+    dt = time.perf_counter() - t0
+    steps = max(2, int(budget_s / max(dt / 2, 1e-6)))
+    steps = min(steps, 5000)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": nodes * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, one {c['nr']}x{c['nz']} case of the workload, {steps} steps "
+                      f"({dt:.1f} s, OpenMP over {cores} host threads)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cases = build_cases(args.workload, "fp64", 0)
+    c = cases[0]
+    nodes = c["nr"] * c["nz"]
+    import oracle
+    from paper_1810_09299_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    o = oracle.Oracle(c).init(W.initial_phi(c))
+    # size each step so that warm-up + timed steps stay within a few minutes
+    t0 = time.perf_counter()
+    o.step(1)
+    per = time.perf_counter() - t0
+    inner = max(1, int(4.0 / max(per, 1e-6)))
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(inner)
+    dt = time.perf_counter() - t0
+    value = nodes * inner * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"{args.workload}: FP64 CPU oracle on case 0 ({c['nr']}x{c['nz']})",
+                       "steps_per_timed_step": inner},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"case 0 of the {args.workload} workload, {inner} oracle steps per "
+                                       f"timed step"},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_cuda(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1810_09299_gb300 import lbm
+    from paper_1810_09299_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = args.precision
+    cases = build_cases(args.workload, prec, rank, args.cases)
+    nodes = sum(c["nr"] * c["nz"] for c in cases)
+    sim = lbm.Simulation(cases)
+    for i, c in enumerate(cases):
+        sim.init_phase(i, c["shape"], c["shape_args"])
+    if args.variant is None:
+        variant = sim.autotune(reps=2)
+    else:
+        variant = args.variant
+        sim.set_variant(variant)
+    flush_buf = None
+    if nodes * BYTES_PER_NODE[prec] < 4 * 129e6:
+        flush_buf = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")
+
+        def flush():
+            flush_buf.fill_(1.0)
+    else:
+        flush = None
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = sim.kernel_launches
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        times = time_steps(sim, torch, args.steps, flush if flush_buf is not None else None)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    launches = sim.kernel_launches - launches0
+    ms = float(np.sum(times))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    total_nodes = nodes * world
+    value = total_nodes * args.steps / (ms * 1e-3) / 1e6
+    d = sim.diagnostics(0)
+    peak, peak_kind = measured_peaks()
+    per_launch_ms = float(np.mean(times))
+    achieved = BYTES_PER_NODE[prec] * nodes / (per_launch_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+        "config": {"workload": {"batched": f"{len(cases)} batched static/oscillating droplet cases (seed 20181022), "
+                                           "grids 64x128..256x512, one launch per step",
+                                "oscillating": "oscillating P2 drop, 128x256, R0=32",
+                                "static": "static drop, 64x128, R=16"}[args.workload],
+                   "precision": prec, "nodes_per_gpu": nodes, "cases_per_gpu": len(cases),
+                   "l2": "flushed between timed steps" if flush_buf is not None else
+                         "inputs larger than L2 (no flush)",
+                   "variant": variant, "parallelism": f"independent cases per GPU x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "note": f"peak {peak_kind}; algorithmic bytes {BYTES_PER_NODE[prec]} B/node x {nodes} nodes "
+                             f"per launch / mean CUDA-event launch duration"},
+        "gpu_launches": int(launches),
+        "stated_error": {"mass": d["mass"], "step": d["step"]},
+    }
+    clocks = clk.summary()
+    if clocks:
+        line["clocks"] = clocks
+    # ---- end to end through the C ABI with host buffers
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e(cases, args, torch)
+    if rank == 0 and not args.no_extra:
+        line["single_case_fp32"] = single_case(torch, "oscillating", "fp32", args.steps)
+        line["single_case_fp64"] = single_case(torch, "oscillating", "fp64", max(4, args.steps // 4))
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(cases[0], budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def e2e(cases, args, torch):
+    """Same metric through the public API with host buffers: host phi0 uploaded
+    (pinned) at the start, then per step one lbm_step and one diagnostics record
+    read back to the host."""
+    from paper_1810_09299_gb300 import lbm
+    from paper_1810_09299_gb300 import workloads as W
+    pinned = [torch.from_numpy(W.initial_phi(c)).pin_memory() for c in cases]
+    phis = [t.numpy() for t in pinned]
+    nodes = sum(c["nr"] * c["nz"] for c in cases)
+    sim = lbm.Simulation(cases)
+    sim.init_phase(0, "host_array", phi=phis[0])
+    for i in range(1, len(cases)):
+        sim.init_phase(i, "host_array", phi=phis[i])
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, c in enumerate(cases):
+        sim.init_phase(i, "host_array", phi=phis[i])
+    for _ in range(args.steps):
+        sim.step(1)
+        sim.diagnostics(0)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    sim.close()
+    h2d = sum(p.nbytes for p in phis) / args.steps
+    return {"value": nodes * args.steps / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": 88}
+
+
+def single_case(torch, workload, prec, steps):
+    from paper_1810_09299_gb300 import lbm
+    cases = build_cases(workload, prec, 0)
+    c = cases[0]
+    sim = lbm.Simulation(c)
+    sim.init_phase(0, c["shape"], c["shape_args"])
+    sim.autotune(reps=3)
+    for _ in range(3):
+        sim.step(1)
+    buf = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")
+    times = time_steps(sim, torch, steps, lambda: buf.fill_(1.0))
+    nodes = c["nr"] * c["nz"]
+    ms = float(np.mean(times))
+    peak, kind = measured_peaks()
+    ach = BYTES_PER_NODE[prec] * nodes / (ms * 1e-3) / 1e9
+    sim.close()
+    return {"workload": f"{workload} {c['nr']}x{c['nz']}", "precision": prec, "value": nodes / (ms * 1e-3) / 1e6,
+            "unit": "MLUPS", "ms_per_step": ms, "l2": "flushed between timed steps",
+            "achieved_gbs": ach, "frac": ach / peak}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "oscillating", "static"])
+    ap.add_argument("--precision", default="mix_fp16", choices=["fp64", "fp32", "mix_fp16", "mix_bf16"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--variant", type=int, default=None, help="step-kernel launch shape (default: autotuned)")
+    ap.add_argument("--cases", type=int, default=512, help="number of batched cases")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cuda(args)
+
+
+if __name__ == "__main__":
+    main()

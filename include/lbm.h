@@ -1,0 +1,205 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) axisymmetric Allen-Cahn phase-field
+ * multiple-relaxation-time lattice Boltzmann library (libaxilbm.so).
+ *
+ * The method is that of Liang et al., "Axisymmetric lattice Boltzmann model for
+ * multiphase flows with large density ratio" (arXiv 1810.09299): a phase-field
+ * LBE for the conservative Allen-Cahn equation (Sec. 2.2, Eq. 9-23) coupled to a
+ * pressure-based hydrodynamic LBE (Sec. 2.3, Eq. 24-37) on a D2Q9 (z, r)
+ * lattice, with the isotropic stencils of Eq. 39-40 for the only non-local
+ * field phi, the axis-symmetry boundary at r = 0 and bounce-back walls.
+ *
+ * Conventions used by every entry point
+ *   - Lattice node (k, j): k = 0..nz-1 along z, j = 0..nr-1 along r.  The first
+ *     lattice line sits at r = 0.5 (Sec. 2.3): r_j = j + 0.5, z_k = k + 0.5.
+ *   - Host arrays are FP64, row-major [z][r] (r fastest), in every precision.
+ *   - Return value: LBM_OK (0) or a negative lbm_status.  Errors are sticky: once
+ *     a call on a handle fails with LBM_ERR_CUDA or LBM_ERR_NONFINITE, every later
+ *     call on that handle returns the same code until lbm_destroy.
+ *   - The library owns all device memory of a handle.  It is allocated
+ *     stream-ordered on the stream given at creation and freed by lbm_destroy.
+ *     Host pointers passed in are borrowed for the duration of the call only.
+ *   - All device work is enqueued on the handle's stream.  Calls that return host
+ *     data (lbm_get_fields, lbm_diagnostics, lbm_get_state, lbm_checkpoint_save)
+ *     synchronise that stream; lbm_step does not.
+ *   - A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef AXILBM_LBM_H
+#define AXILBM_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_sim lbm_handle;   /* one case, or a batch of cases */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = -1,  /* a parameter is out of range or a pointer is NULL */
+    LBM_ERR_CUDA = -2,         /* a CUDA runtime call or a kernel launch failed */
+    LBM_ERR_NONFINITE = -3,    /* a NaN or Inf appeared in phi, u or p */
+    LBM_ERR_TIMEOUT = -4,      /* a bounded device wait gave up */
+    LBM_ERR_OOM = -5,          /* device allocation failed */
+    LBM_ERR_STATE = -6         /* call out of order (e.g. lbm_step before lbm_init_phase) */
+} lbm_status;
+
+/* Storage and arithmetic precision of a handle.
+ *   LBM_FP64      populations and arithmetic in FP64.
+ *   LBM_FP32      populations and arithmetic in FP32.
+ *   LBM_MIX_FP16  populations f_1..8 and g_0..8 stored as FP16 deviations
+ *                 (f_i / (w_i r) - 1/2 and g_i / (w_i r), r of the storing node),
+ *                 f_0 stored in FP32 so that each node's outgoing population sum is
+ *                 kept exactly; arithmetic in FP32; reductions in FP64.
+ *   LBM_MIX_BF16  as LBM_MIX_FP16 with bfloat16 storage. */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_MIX_FP16 = 2, LBM_MIX_BF16 = 3 } lbm_precision;
+
+/* Coupling of the pressure p and the radial velocity u_r (Eq. 32 uses p, Eq. 33
+ * computes p from u).  LBM_P_EXACT solves both together at each node (the pair is
+ * a quadratic in p; the root continuous with the linear solution is taken).
+ * LBM_P_LAGGED uses p^{n-1} in Eq. 32 and Eq. 30. */
+typedef enum { LBM_P_EXACT = 0, LBM_P_LAGGED = 1 } lbm_p_coupling;
+
+/* Parameters of one case.
+ *   nr, nz       lattice size (nr >= 2, nz >= 2).
+ *   z_periodic   1: periodic in z; 0: halfway bounce-back walls at z = 0 and z = nz.
+ *                The wall at r = nr is always a halfway bounce-back wall and the
+ *                axis r = 0 always a symmetry line (Sec. 2.3).
+ *   rho_l, rho_g liquid (phi = 1) and gas (phi = 0) densities, Eq. 17 (> 0).
+ *   nu_l, nu_g   kinematic viscosities, Eq. 35 (> 0).
+ *   sigma, W     surface tension and interface width: k = 1.5 sigma W and
+ *                beta = 12 sigma / W in Eq. 4 (sigma >= 0, W > 0).
+ *   mobility     M of Eq. 1 and Eq. 11; tau_f = M / cs2 + 1/2 (Eq. 18) (> 0).
+ *   grav_z       z component of gravity; body force G = ((rho - rho_l) grav_z, 0).
+ *   sf[9], sg[9] diagonal MRT rates of Eq. 13 and Eq. 28, each in [0, 2).  A
+ *                negative entry is derived: sf -> 1/tau_f, sg -> 1/tau_g(x) with
+ *                nu(x) = cs2 (tau_g - 1/2) at every node (Eq. 34).
+ *   n_eps        interface normal n = grad phi / (|grad phi| + n_eps).
+ *   precision    lbm_precision; p_coupling lbm_p_coupling. */
+typedef struct {
+    int32_t nr, nz, z_periodic;
+    int32_t precision;
+    int32_t p_coupling;
+    int32_t reserved;
+    double rho_l, rho_g, nu_l, nu_g, sigma, W, mobility, grav_z;
+    double sf[9], sg[9];
+    double n_eps;
+} lbm_params;
+
+/* Diagnostics record, all FP64, computed on the device with compensated
+ * (Neumaier) sums in a fixed order (deterministic).
+ *   mass               sum over nodes of r phi (equal to the sum of all f_i).
+ *   kinetic            sum of 0.5 r rho |u|^2.
+ *   z_centroid         sum r z phi / sum r phi.
+ *   dp                 <p> over phi > 0.99 minus <p> over phi < 0.01 (r-weighted).
+ *   umax               max |u|.
+ *   axis_half_length   half the length of the phi > 1/2 set on the axis row j = 0,
+ *                      from linear interpolation of the crossings.
+ *   radial_half_length first phi = 1/2 crossing along r on the row nearest z_centroid.
+ *   nonfinite          number of nodes with a non-finite phi, u or p. */
+typedef struct {
+    double step, mass, kinetic, z_centroid, dp, umax, phi_min, phi_max;
+    double axis_half_length, radial_half_length, nonfinite;
+} lbm_diag;
+
+/* Initial phase-field shapes for lbm_init_phase (coordinates z = k+0.5, r = j+0.5).
+ *   FLAT      args {z_i, W, axis}: phi = 1/2 + 1/2 tanh(2 (z_i - x) / W), x = z (axis 0) or r.
+ *   SPHERE    args {z_c, R, W}: drop of Eq. 41, phi = 1/2 + 1/2 tanh(2 (R - d) / W).
+ *   ELLIPSOID args {z_c, R_z, R_r, W}: Eq. 46 with R_e = (R_r^2 R_z)^(1/3).
+ *   P2        args {z_c, R0, eps, W}: drop of radius R0 (1 + eps P2(cos theta)).
+ *   THREAD    args {R, amp, lambda, theta, W}: Eq. 47 with d = amp cos(2 pi z / lambda + theta).
+ *   BUBBLE    args {z_c, R, W}: 1 - SPHERE.
+ *   HOST_ARRAY host_phi [nz][nr] is copied to the device. */
+typedef enum {
+    LBM_SHAPE_FLAT = 0, LBM_SHAPE_SPHERE = 1, LBM_SHAPE_ELLIPSOID = 2, LBM_SHAPE_P2 = 3,
+    LBM_SHAPE_THREAD = 4, LBM_SHAPE_BUBBLE = 5, LBM_SHAPE_HOST_ARRAY = 6
+} lbm_shape;
+
+/* Field selection bits for lbm_get_fields; fields are written in bit order. */
+enum { LBM_FIELD_PHI = 1, LBM_FIELD_RHO = 2, LBM_FIELD_UZ = 4, LBM_FIELD_UR = 8, LBM_FIELD_P = 16 };
+
+/* Create a single-case handle.  stream: a cudaStream_t (NULL = default stream).
+ * Validates the parameters (LBM_ERR_INVALID_ARG), allocates the device state
+ * (LBM_ERR_OOM) and selects the current CUDA device.  *out is set on success. */
+int lbm_create(const lbm_params* prm, void* stream, lbm_handle** out);
+
+/* Create a batch of ncases independent cases (ncases >= 1) that advance together:
+ * each lbm_step launch covers the tiles of every case (Sec. 3's test problems run
+ * side by side).  All cases must share one precision. */
+int lbm_batch_create(const lbm_params* cases, int32_t ncases, void* stream, lbm_handle** out);
+
+/* Number of cases of a handle (1 for lbm_create). */
+int32_t lbm_num_cases(const lbm_handle* h);
+
+/* Initial condition of case `icase` (Sec. 3, the paper is silent beyond phi):
+ * phi0 from the shape, u = 0, p = 0, f = f^eq(phi0, u = 0) (Eq. 11), g = 0
+ * (= g^eq at p = 0, u = 0, Eq. 25), chi^{-1} = (0, M phi0) so that the first
+ * time derivative of Eq. 38 is zero, p^{-1} = 0.  Resets the step counter.
+ * nargs must match the shape (see lbm_shape); host_phi is used only for
+ * LBM_SHAPE_HOST_ARRAY.  lbm_init_phase initialises case 0. */
+int lbm_init_phase(lbm_handle* h, int32_t shape, const double* shape_args, int32_t nargs,
+                   const double* host_phi);
+int lbm_case_init_phase(lbm_handle* h, int32_t icase, int32_t shape, const double* shape_args,
+                        int32_t nargs, const double* host_phi);
+
+/* Advance every case by nsteps time steps (nsteps >= 0).  One step is
+ * Eq. 16 (phi) -> Eq. 39-40 (stencils) -> Eq. 4, 17, 35 -> Eq. 32-33 (u, p) ->
+ * Eq. 30 (force) -> Eq. 19-23 (phase-field collision) -> Eq. 24-29, 36-37
+ * (hydrodynamic collision) -> Eq. 20 (streaming with axis reflection and
+ * bounce-back).  Asynchronous on the handle's stream; repeated steps are
+ * replayed from a captured CUDA graph.  Returns launch errors immediately and
+ * earlier sticky errors. */
+int lbm_step(lbm_handle* h, int64_t nsteps);
+
+/* Copy macroscopic fields of case 0 / case icase to the host:
+ * host_out holds popcount(mask) arrays of [nz][nr] doubles, in bit order of
+ * LBM_FIELD_*.  u and p are recomputed from the current populations exactly as
+ * the next step would compute them.  Synchronises. */
+int lbm_get_fields(lbm_handle* h, int32_t mask, double* host_out);
+int lbm_case_get_fields(lbm_handle* h, int32_t icase, int32_t mask, double* host_out);
+
+/* Diagnostics of case 0 / case icase (see lbm_diag).  Synchronises.  Returns
+ * LBM_ERR_NONFINITE (and fills *out) if any phi, u or p is not finite. */
+int lbm_diagnostics(lbm_handle* h, lbm_diag* out);
+int lbm_case_diagnostics(lbm_handle* h, int32_t icase, lbm_diag* out);
+
+/* Populations of case icase as FP64 host arrays f[9][nz][nr], g[9][nz][nr] and the
+ * time-level state aux[3][nz][nr] = (chi_z^{n-1}, chi_r^{n-1}, p^{n-1}); any pointer
+ * may be NULL.  lbm_set_state writes them (encoding to the storage precision).
+ * Synchronises. */
+int lbm_get_state(lbm_handle* h, int32_t icase, double* f, double* g, double* aux);
+int lbm_set_state(lbm_handle* h, int32_t icase, const double* f, const double* g, const double* aux);
+
+/* Checkpoint / resume of the whole handle in its native storage precision.
+ * lbm_checkpoint_size returns the byte size of the image; save/load copy it
+ * to / from host memory of at least that size.  Resuming from a checkpoint is
+ * bit-identical to running straight through.  Synchronises. */
+int64_t lbm_checkpoint_size(const lbm_handle* h);
+int lbm_checkpoint_save(lbm_handle* h, void* host_buf);
+int lbm_checkpoint_load(lbm_handle* h, const void* host_buf);
+
+/* Time a few launch shapes of the step kernel on the current state (which is
+ * saved and restored, so the simulation does not advance) and keep the fastest.
+ * reps >= 1 timed steps per candidate.  Writes the chosen variant index to
+ * *chosen (may be NULL).  Synchronises. */
+int lbm_autotune(lbm_handle* h, int32_t reps, int32_t* chosen);
+
+/* Select a step-kernel launch variant explicitly (0 .. lbm_num_variants()-1). */
+int lbm_set_variant(lbm_handle* h, int32_t variant);
+int32_t lbm_num_variants(void);
+
+/* Number of step-kernel launches this handle has issued (one per step). */
+int64_t lbm_kernel_launches(const lbm_handle* h);
+
+/* Release every resource of the handle (NULL is ignored). */
+int lbm_destroy(lbm_handle* h);
+
+/* Static description of a status code. */
+const char* lbm_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

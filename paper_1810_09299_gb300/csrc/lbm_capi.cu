@@ -1,0 +1,662 @@
+// lbm_capi.cu -- the C ABI of include/lbm.h: handle life cycle, device memory,
+// step scheduling (direct launches and captured CUDA graphs), field and
+// diagnostics read-back, state transfer, checkpoints and the launch-shape
+// autotuner.  All numerical work is done by the kernels in lbm_kernels.cuh and
+// lbm_diag.cu; this file only validates, allocates, launches and copies.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+using namespace axilbm;
+
+namespace {
+
+constexpr int kGraphSteps = 32;  // steps per captured graph (even: parity returns)
+
+size_t pt_size(int prec) { return prec == LBM_FP64 ? 8 : (prec == LBM_FP32 ? 4 : 2); }
+size_t f0_size(int) { return 8; }  // f_0 is FP64 in every precision (mass ledger)
+size_t real_size(int prec) { return prec == LBM_FP64 ? 8 : 4; }
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+int validate(const lbm_params& p) {
+    if (p.nr < 2 || p.nz < 2) return LBM_ERR_INVALID_ARG;
+    if ((int64_t)p.nr * p.nz > (int64_t)1 << 34) return LBM_ERR_INVALID_ARG;
+    if (p.z_periodic != 0 && p.z_periodic != 1) return LBM_ERR_INVALID_ARG;
+    if (p.precision < LBM_FP64 || p.precision > LBM_MIX_BF16) return LBM_ERR_INVALID_ARG;
+    if (p.p_coupling != LBM_P_EXACT && p.p_coupling != LBM_P_LAGGED) return LBM_ERR_INVALID_ARG;
+    if (!finite_pos(p.rho_l) || !finite_pos(p.rho_g) || !finite_pos(p.nu_l) || !finite_pos(p.nu_g))
+        return LBM_ERR_INVALID_ARG;
+    if (!finite_pos(p.W) || !finite_pos(p.mobility)) return LBM_ERR_INVALID_ARG;
+    if (!std::isfinite(p.sigma) || p.sigma < 0.0 || !std::isfinite(p.grav_z)) return LBM_ERR_INVALID_ARG;
+    if (!std::isfinite(p.n_eps) || p.n_eps < 0.0) return LBM_ERR_INVALID_ARG;
+    for (int i = 0; i < 9; ++i) {
+        for (double s : {p.sf[i], p.sg[i]}) {
+            if (!std::isfinite(s)) return LBM_ERR_INVALID_ARG;
+            if (s >= 0.0 && s >= 2.0) return LBM_ERR_INVALID_ARG;
+        }
+    }
+    return LBM_OK;
+}
+
+int nargs_of(int shape) {
+    switch (shape) {
+        case LBM_SHAPE_FLAT: return 3;
+        case LBM_SHAPE_SPHERE: return 3;
+        case LBM_SHAPE_ELLIPSOID: return 4;
+        case LBM_SHAPE_P2: return 4;
+        case LBM_SHAPE_THREAD: return 5;
+        case LBM_SHAPE_BUBBLE: return 3;
+        case LBM_SHAPE_HOST_ARRAY: return 0;
+        default: return -1;
+    }
+}
+
+}  // namespace
+
+struct lbm_sim {
+    int device = 0;
+    int precision = 0;
+    int ncases = 0;
+    cudaStream_t stream = nullptr;      // caller's stream
+    cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
+    std::vector<lbm_params> prm;
+    std::vector<CaseDev> cases;
+    std::vector<int64_t> case_steps;
+    std::vector<char> initialized;
+    DeviceState D{};
+    // tiles: one list per step variant over all cases, plus the 8-row tiling
+    // of each case for the field kernel
+    TileDev* tiles_d[kNumVariants] = {};
+    int ntiles[kNumVariants] = {};
+    std::vector<TileDev*> ftiles_d;
+    std::vector<int> nftiles;
+    int64_t max_nodes = 0;  // largest nz * nr of a case
+    double* fields = nullptr;   // [5][nz][nr] of the largest case
+    double* phi0 = nullptr;     // [nz][nr]
+    double* state = nullptr;    // [21][nz][nr]
+    double* partials = nullptr;
+    double* diag_out = nullptr;
+    std::vector<void*> allocations;
+    int parity = 0;
+    int variant = 0;
+    int sticky = LBM_OK;
+    int64_t launches = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_variant = -1;
+};
+
+namespace {
+
+int fail(lbm_sim* h, int code) {
+    if (code == LBM_ERR_CUDA || code == LBM_ERR_NONFINITE) h->sticky = code;
+    return code;
+}
+
+int cuda_ok(lbm_sim* h, cudaError_t e) {
+    if (e == cudaSuccess) return LBM_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return LBM_ERR_OOM;
+    }
+    return fail(h, LBM_ERR_CUDA);
+}
+
+cudaError_t dev_alloc(lbm_sim* h, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = cudaMallocAsync(p, bytes, h->stream);
+    if (e != cudaSuccess) return e;
+    h->allocations.push_back(*p);
+    return cudaMemsetAsync(*p, 0, bytes, h->stream);
+}
+
+cudaError_t launch_step_any(lbm_sim* h, int parity, int variant, cudaStream_t st) {
+    const TileDev* t = h->tiles_d[variant];
+    const int n = h->ntiles[variant];
+    switch (h->precision) {
+        case LBM_FP64: return launch_step_f64(h->D, parity, variant, t, n, st);
+        case LBM_FP32: return launch_step_f32(h->D, parity, variant, t, n, st);
+        case LBM_MIX_FP16: return launch_step_h16(h->D, parity, variant, t, n, st);
+        default: return launch_step_b16(h->D, parity, variant, t, n, st);
+    }
+}
+
+cudaError_t launch_fields_any(lbm_sim* h, int icase) {
+    const TileDev* t = h->ftiles_d[icase];
+    const int n = h->nftiles[icase];
+    switch (h->precision) {
+        case LBM_FP64: return launch_fields_f64(h->D, h->parity, t, n, h->fields, h->stream);
+        case LBM_FP32: return launch_fields_f32(h->D, h->parity, t, n, h->fields, h->stream);
+        case LBM_MIX_FP16: return launch_fields_h16(h->D, h->parity, t, n, h->fields, h->stream);
+        default: return launch_fields_b16(h->D, h->parity, t, n, h->fields, h->stream);
+    }
+}
+
+cudaError_t launch_init_any(lbm_sim* h, int icase) {
+    const CaseDev& C = h->cases[icase];
+    switch (h->precision) {
+        case LBM_FP64: return launch_init_f64(h->D, h->parity, C, h->phi0, h->stream);
+        case LBM_FP32: return launch_init_f32(h->D, h->parity, C, h->phi0, h->stream);
+        case LBM_MIX_FP16: return launch_init_h16(h->D, h->parity, C, h->phi0, h->stream);
+        default: return launch_init_b16(h->D, h->parity, C, h->phi0, h->stream);
+    }
+}
+
+cudaError_t launch_get_state_any(lbm_sim* h, int icase, double* f, double* g, double* aux) {
+    const CaseDev& C = h->cases[icase];
+    switch (h->precision) {
+        case LBM_FP64: return launch_get_state_f64(h->D, h->parity, C, f, g, aux, h->stream);
+        case LBM_FP32: return launch_get_state_f32(h->D, h->parity, C, f, g, aux, h->stream);
+        case LBM_MIX_FP16: return launch_get_state_h16(h->D, h->parity, C, f, g, aux, h->stream);
+        default: return launch_get_state_b16(h->D, h->parity, C, f, g, aux, h->stream);
+    }
+}
+
+cudaError_t launch_set_state_any(lbm_sim* h, int icase, const double* f, const double* g, const double* aux) {
+    const CaseDev& C = h->cases[icase];
+    switch (h->precision) {
+        case LBM_FP64: return launch_set_state_f64(h->D, h->parity, C, f, g, aux, h->stream);
+        case LBM_FP32: return launch_set_state_f32(h->D, h->parity, C, f, g, aux, h->stream);
+        case LBM_MIX_FP16: return launch_set_state_h16(h->D, h->parity, C, f, g, aux, h->stream);
+        default: return launch_set_state_b16(h->D, h->parity, C, f, g, aux, h->stream);
+    }
+}
+
+template <typename Real>
+void fill_params(CaseReal<Real>& P, const lbm_params& p) {
+    P.rho_l = (Real)p.rho_l;
+    P.rho_g = (Real)p.rho_g;
+    P.nu_l = (Real)p.nu_l;
+    P.nu_g = (Real)p.nu_g;
+    P.grav_z = (Real)p.grav_z;
+    P.n_eps = (Real)p.n_eps;
+    P.beta = (Real)(12.0 * p.sigma / p.W);  // Eq. 4
+    P.kappa = (Real)(1.5 * p.sigma * p.W);
+    P.inv_W = (Real)(1.0 / p.W);
+    P.mob = (Real)p.mobility;
+    const double inv_tau_f = 1.0 / (p.mobility * 3.0 + 0.5);  // Eq. 18
+    for (int i = 0; i < 9; ++i) {
+        P.sf[i] = (Real)(p.sf[i] < 0.0 ? inv_tau_f : p.sf[i]);
+        P.sg[i] = (Real)(p.sg[i] < 0.0 ? 0.0 : p.sg[i]);
+    }
+}
+
+CaseDev make_case(const lbm_params& p, int64_t off) {
+    CaseDev C{};
+    C.nr = p.nr;
+    C.nz = p.nz;
+    C.pitch = (p.nr + 31) / 32 * 32;
+    C.zper = p.z_periodic;
+    C.p_coupling = p.p_coupling;
+    C.off = off;
+    C.sg_local = 0;
+    for (int i = 0; i < 9; ++i)
+        if (p.sg[i] < 0.0) C.sg_local |= 1u << i;
+    fill_params<double>(C.pd, p);
+    fill_params<float>(C.pf, p);
+    return C;
+}
+
+std::vector<TileDev> make_tiles(const std::vector<CaseDev>& cs, int tz, int only_case) {
+    std::vector<TileDev> t;
+    for (int c = 0; c < (int)cs.size(); ++c) {
+        if (only_case >= 0 && c != only_case) continue;
+        for (int k0 = 0; k0 < cs[c].nz; k0 += tz)
+            for (int j0 = 0; j0 < cs[c].nr; j0 += 32) t.push_back(TileDev{c, k0, j0, 0});
+    }
+    return t;
+}
+
+int upload_tiles(lbm_sim* h, const std::vector<TileDev>& t, TileDev** out) {
+    void* p = nullptr;
+    cudaError_t e = dev_alloc(h, &p, std::max<size_t>(1, t.size()) * sizeof(TileDev));
+    if (e != cudaSuccess) return cuda_ok(h, e);
+    if (!t.empty()) {
+        e = cudaMemcpyAsync(p, t.data(), t.size() * sizeof(TileDev), cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_ok(h, e);
+    }
+    *out = (TileDev*)p;
+    return LBM_OK;
+}
+
+void release(lbm_sim* h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    for (void* p : h->allocations) cudaFreeAsync(p, h->stream);
+    h->allocations.clear();
+    cudaStreamSynchronize(h->stream);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
+}
+
+int create_impl(const lbm_params* cases, int32_t n, void* stream, lbm_handle** out) {
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!cases || n < 1) return LBM_ERR_INVALID_ARG;
+    for (int c = 0; c < n; ++c) {
+        int v = validate(cases[c]);
+        if (v != LBM_OK) return v;
+        if (cases[c].precision != cases[0].precision) return LBM_ERR_INVALID_ARG;
+    }
+    lbm_sim* h = new (std::nothrow) lbm_sim();
+    if (!h) return LBM_ERR_OOM;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return LBM_ERR_CUDA;
+    }
+    h->stream = (cudaStream_t)stream;
+    h->precision = cases[0].precision;
+    h->ncases = n;
+    h->prm.assign(cases, cases + n);
+    int64_t off = 0;
+    for (int c = 0; c < n; ++c) {
+        h->cases.push_back(make_case(cases[c], off));
+        off += (int64_t)h->cases[c].nz * h->cases[c].pitch;
+        h->max_nodes = std::max<int64_t>(h->max_nodes, (int64_t)cases[c].nz * cases[c].nr);
+    }
+    h->D.total = off;
+    h->case_steps.assign(n, 0);
+    h->initialized.assign(n, 0);
+    int rc = LBM_OK;
+    auto A = [&](void** p, size_t bytes) {
+        if (rc != LBM_OK) return;
+        cudaError_t e = dev_alloc(h, p, bytes);
+        if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? LBM_ERR_OOM : LBM_ERR_CUDA;
+    };
+    const size_t T = (size_t)off;
+    for (int b = 0; b < 2; ++b) {
+        A(&h->D.f0[b], T * f0_size(h->precision));
+        A(&h->D.fq[b], 8 * T * pt_size(h->precision));
+        A(&h->D.g[b], 9 * T * pt_size(h->precision));
+    }
+    A(&h->D.chi_z, T * real_size(h->precision));
+    A(&h->D.chi_r, T * real_size(h->precision));
+    A(&h->D.p_prev, T * real_size(h->precision));
+    A(&h->D.cases, n * sizeof(CaseDev));
+    A((void**)&h->fields, 5 * (size_t)h->max_nodes * sizeof(double));
+    A((void**)&h->phi0, (size_t)h->max_nodes * sizeof(double));
+    A((void**)&h->state, 21 * (size_t)h->max_nodes * sizeof(double));
+    A((void**)&h->partials, diag_partials_size() * sizeof(double));
+    A((void**)&h->diag_out, 16 * sizeof(double));
+    if (rc == LBM_OK) {
+        cudaError_t e = cudaMemcpyAsync(h->D.cases, h->cases.data(), n * sizeof(CaseDev), cudaMemcpyHostToDevice,
+                                        h->stream);
+        if (e != cudaSuccess) rc = LBM_ERR_CUDA;
+    }
+    for (int v = 0; v < kNumVariants && rc == LBM_OK; ++v) {
+        std::vector<TileDev> t = make_tiles(h->cases, kVariantTZ[v], -1);
+        h->ntiles[v] = (int)t.size();
+        rc = upload_tiles(h, t, &h->tiles_d[v]);
+    }
+    for (int c = 0; c < n && rc == LBM_OK; ++c) {
+        std::vector<TileDev> t = make_tiles(h->cases, 8, c);
+        TileDev* d = nullptr;
+        rc = upload_tiles(h, t, &d);
+        h->ftiles_d.push_back(d);
+        h->nftiles.push_back((int)t.size());
+    }
+    if (rc == LBM_OK && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        rc = LBM_ERR_CUDA;
+    if (rc == LBM_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+    if (rc != LBM_OK) {
+        cudaGetLastError();
+        release(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+int enter(lbm_sim* h) {
+    if (!h) return LBM_ERR_INVALID_ARG;
+    if (h->sticky != LBM_OK) return h->sticky;
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(h, LBM_ERR_CUDA);
+    return LBM_OK;
+}
+
+int capture_graph(lbm_sim* h) {
+    if (h->graph && h->graph_variant == h->variant) return LBM_OK;
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return fail(h, LBM_ERR_CUDA);
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < kGraphSteps && e == cudaSuccess; ++s) e = launch_step_any(h, s & 1, h->variant, h->cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(h, LBM_ERR_CUDA);
+    }
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return fail(h, LBM_ERR_CUDA);
+    }
+    h->graph_variant = h->variant;
+    return LBM_OK;
+}
+
+int step_direct(lbm_sim* h, int64_t n) {
+    for (int64_t s = 0; s < n; ++s) {
+        cudaError_t e = launch_step_any(h, h->parity, h->variant, h->stream);
+        if (e != cudaSuccess) return cuda_ok(h, e);
+        h->parity ^= 1;
+        h->launches += 1;
+    }
+    return LBM_OK;
+}
+
+int check_case(lbm_sim* h, int icase) {
+    if (icase < 0 || icase >= h->ncases) return LBM_ERR_INVALID_ARG;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_create(const lbm_params* prm, void* stream, lbm_handle** out) { return create_impl(prm, 1, stream, out); }
+
+int lbm_batch_create(const lbm_params* cases, int32_t ncases, void* stream, lbm_handle** out) {
+    return create_impl(cases, ncases, stream, out);
+}
+
+int32_t lbm_num_cases(const lbm_handle* h) { return h ? h->ncases : 0; }
+
+int lbm_case_init_phase(lbm_handle* h, int32_t icase, int32_t shape, const double* shape_args, int32_t nargs,
+                        const double* host_phi) {
+    int rc = enter(h);
+    if (rc != LBM_OK) return rc;
+    if (check_case(h, icase) != LBM_OK) return LBM_ERR_INVALID_ARG;
+    const int need = nargs_of(shape);
+    if (need < 0) return LBM_ERR_INVALID_ARG;
+    const lbm_params& p = h->prm[icase];
+    const int64_t n = (int64_t)p.nz * p.nr;
+    if (shape == LBM_SHAPE_HOST_ARRAY) {
+        if (!host_phi) return LBM_ERR_INVALID_ARG;
+        rc = cuda_ok(h, cudaMemcpyAsync(h->phi0, host_phi, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    } else {
+        if (nargs != need || !shape_args) return LBM_ERR_INVALID_ARG;
+        for (int i = 0; i < nargs; ++i)
+            if (!std::isfinite(shape_args[i])) return LBM_ERR_INVALID_ARG;
+        rc = cuda_ok(h, launch_shape(shape, shape_args, nargs, p.nz, p.nr, h->phi0, h->stream));
+    }
+    if (rc != LBM_OK) return rc;
+    rc = cuda_ok(h, launch_init_any(h, icase));
+    if (rc != LBM_OK) return rc;
+    h->case_steps[icase] = 0;
+    h->initialized[icase] = 1;
+    return cuda_ok(h, cudaStreamSynchronize(h->stream));
+}
+
+int lbm_init_phase(lbm_handle* h, int32_t shape, const double* shape_args, int32_t nargs, const double* host_phi) {
+    return lbm_case_init_phase(h, 0, shape, shape_args, nargs, host_phi);
+}
+
+int lbm_step(lbm_handle* h, int64_t nsteps) {
+    int rc = enter(h);
+    if (rc != LBM_OK) return rc;
+    if (nsteps < 0) return LBM_ERR_INVALID_ARG;
+    for (int c = 0; c < h->ncases; ++c)
+        if (!h->initialized[c]) return LBM_ERR_STATE;
+    if (nsteps == 0) return LBM_OK;
+    int64_t left = nsteps;
+    if (left >= kGraphSteps) {
+        if (h->parity == 1) {
+            rc = step_direct(h, 1);
+            if (rc != LBM_OK) return rc;
+            left -= 1;
+        }
+        if (left >= kGraphSteps) {
+            rc = capture_graph(h);
+            if (rc != LBM_OK) return rc;
+            while (left >= kGraphSteps) {
+                cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
+                if (e != cudaSuccess) return cuda_ok(h, e);
+                left -= kGraphSteps;
+                h->launches += kGraphSteps;
+            }
+        }
+    }
+    rc = step_direct(h, left);
+    if (rc != LBM_OK) return rc;
+    for (int c = 0; c < h->ncases; ++c) h->case_steps[c] += nsteps;
+    return LBM_OK;
+}
+
+int lbm_case_get_fields(lbm_handle* h, int32_t icase, int32_t mask, double* host_out) {
+    int rc = enter(h);
+    if (rc != LBM_OK) return rc;
+    if (check_case(h, icase) != LBM_OK || !host_out || mask <= 0 || mask > 31) return LBM_ERR_INVALID_ARG;
+    if (!h->initialized[icase]) return LBM_ERR_STATE;
+    rc = cuda_ok(h, launch_fields_any(h, icase));
+    if (rc != LBM_OK) return rc;
+    const int64_t n = (int64_t)h->prm[icase].nz * h->prm[icase].nr;
+    int slot = 0;
+    for (int b = 0; b < 5; ++b) {
+        if (!(mask & (1 << b))) continue;
+        rc = cuda_ok(h, cudaMemcpyAsync(host_out + slot * n, h->fields + b * n, n * sizeof(double),
+                                        cudaMemcpyDeviceToHost, h->stream));
+        if (rc != LBM_OK) return rc;
+        ++slot;
+    }
+    return cuda_ok(h, cudaStreamSynchronize(h->stream));
+}
+
+int lbm_get_fields(lbm_handle* h, int32_t mask, double* host_out) { return lbm_case_get_fields(h, 0, mask, host_out); }
+
+int lbm_case_diagnostics(lbm_handle* h, int32_t icase, lbm_diag* out) {
+    int rc = enter(h);
+    if (rc != LBM_OK) return rc;
+    if (check_case(h, icase) != LBM_OK || !out) return LBM_ERR_INVALID_ARG;
+    if (!h->initialized[icase]) return LBM_ERR_STATE;
+    rc = cuda_ok(h, launch_fields_any(h, icase));
+    if (rc != LBM_OK) return rc;
+    const lbm_params& p = h->prm[icase];
+    rc = cuda_ok(h, launch_diag(h->fields, p.nz, p.nr, p.z_periodic, (double)h->case_steps[icase], h->partials,
+                                h->diag_out, h->stream));
+    if (rc != LBM_OK) return rc;
+    double buf[11];
+    rc = cuda_ok(h, cudaMemcpyAsync(buf, h->diag_out, sizeof(buf), cudaMemcpyDeviceToHost, h->stream));
+    if (rc != LBM_OK) return rc;
+    rc = cuda_ok(h, cudaStreamSynchronize(h->stream));
+    if (rc != LBM_OK) return rc;
+    static_assert(sizeof(lbm_diag) == sizeof(buf), "diag layout");
+    std::memcpy(out, buf, sizeof(buf));
+    if (out->nonfinite > 0) return fail(h, LBM_ERR_NONFINITE);
+    return LBM_OK;
+}
+
+int lbm_diagnostics(lbm_handle* h, lbm_diag* out) { return lbm_case_diagnostics(h, 0, out); }
+
+int lbm_get_state(lbm_handle* h, int32_t icase, double* f, double* g, double* aux) {
+    int rc = enter(h);
+    if (rc != LBM_OK) return rc;
+    if (check_case(h, icase) != LBM_OK) return LBM_ERR_INVALID_ARG;
+    const int64_t n = (int64_t)h->prm[icase].nz * h->prm[icase].nr;
+    double* df = h->state;
+    double* dg = h->state + 9 * n;
+    double* da = h->state + 18 * n;
+    rc = cuda_ok(h, launch_get_state_any(h, icase, f ? df : nullptr, g ? dg : nullptr, aux ? da : nullptr));
+    if (rc != LBM_OK) return rc;
+    if (f) rc = cuda_ok(h, cudaMemcpyAsync(f, df, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (rc == LBM_OK && g)
+        rc = cuda_ok(h, cudaMemcpyAsync(g, dg, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (rc == LBM_OK && aux)
+        rc = cuda_ok(h, cudaMemcpyAsync(aux, da, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (rc != LBM_OK) return rc;
+    return cuda_ok(h, cudaStreamSynchronize(h->stream));
+}
+
+int lbm_set_state(lbm_handle* h, int32_t icase, const double* f, const double* g, const double* aux) {
+    int rc = enter(h);
+    if (rc != LBM_OK) return rc;
+    if (check_case(h, icase) != LBM_OK) return LBM_ERR_INVALID_ARG;
+    const int64_t n = (int64_t)h->prm[icase].nz * h->prm[icase].nr;
+    double* df = h->state;
+    double* dg = h->state + 9 * n;
+    double* da = h->state + 18 * n;
+    if (f) rc = cuda_ok(h, cudaMemcpyAsync(df, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (rc == LBM_OK && g)
+        rc = cuda_ok(h, cudaMemcpyAsync(dg, g, 9 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (rc == LBM_OK && aux)
+        rc = cuda_ok(h, cudaMemcpyAsync(da, aux, 3 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (rc != LBM_OK) return rc;
+    rc = cuda_ok(h, launch_set_state_any(h, icase, f ? df : nullptr, g ? dg : nullptr, aux ? da : nullptr));
+    if (rc != LBM_OK) return rc;
+    if (f) h->initialized[icase] = 1;
+    return cuda_ok(h, cudaStreamSynchronize(h->stream));
+}
+
+int64_t lbm_checkpoint_size(const lbm_handle* h) {
+    if (!h) return -1;
+    const int64_t T = h->D.total;
+    const int p = h->precision;
+    return (int64_t)(T * (f0_size(p) + 17 * pt_size(p) + 3 * real_size(p))) + 8 * (int64_t)h->ncases;
+}
+
+namespace {
+// Copy the current state (the buffers the next step reads, chi, p^{n-1}) to or
+// from `buf` (host memory, or device memory when `device` is set).
+int checkpoint_copy(lbm_sim* h, void* buf, bool save, bool device = false) {
+    const int64_t T = h->D.total;
+    const int p = h->precision;
+    const int a = h->parity;
+    struct Part {
+        void* dev;
+        size_t bytes;
+    } parts[] = {{h->D.f0[a], T * f0_size(p)},     {h->D.fq[a], 8 * T * pt_size(p)},
+                 {h->D.g[a], 9 * T * pt_size(p)},   {h->D.chi_z, T * real_size(p)},
+                 {h->D.chi_r, T * real_size(p)},    {h->D.p_prev, T * real_size(p)}};
+    char* cur = (char*)buf;
+    for (const Part& q : parts) {
+        const cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice
+                                           : (save ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+        cudaError_t e = save ? cudaMemcpyAsync(cur, q.dev, q.bytes, kind, h->stream)
+                             : cudaMemcpyAsync(q.dev, cur, q.bytes, kind, h->stream);
+        if (e != cudaSuccess) return cuda_ok(h, e);
+        cur += q.bytes;
+    }
+    if (!device) {
+        if (save) std::memcpy(cur, h->case_steps.data(), 8 * h->ncases);
+        else {
+            std::memcpy(h->case_steps.data(), cur, 8 * h->ncases);
+            for (int c = 0; c < h->ncases; ++c) h->initialized[c] = 1;
+        }
+    }
+    return cuda_ok(h, cudaStreamSynchronize(h->stream));
+}
+}  // namespace
+
+int lbm_checkpoint_save(lbm_handle* h, void* host_buf) {
+    int rc = enter(h);
+    if (rc != LBM_OK) return rc;
+    if (!host_buf) return LBM_ERR_INVALID_ARG;
+    return checkpoint_copy(h, host_buf, true);
+}
+
+int lbm_checkpoint_load(lbm_handle* h, const void* host_buf) {
+    int rc = enter(h);
+    if (rc != LBM_OK) return rc;
+    if (!host_buf) return LBM_ERR_INVALID_ARG;
+    return checkpoint_copy(h, const_cast<void*>(host_buf), false);
+}
+
+int32_t lbm_num_variants(void) { return kNumVariants; }
+
+int lbm_set_variant(lbm_handle* h, int32_t variant) {
+    int rc = enter(h);
+    if (rc != LBM_OK) return rc;
+    if (variant < 0 || variant >= kNumVariants) return LBM_ERR_INVALID_ARG;
+    h->variant = variant;
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_handle* h, int32_t reps, int32_t* chosen) {
+    int rc = enter(h);
+    if (rc != LBM_OK) return rc;
+    if (reps < 1) return LBM_ERR_INVALID_ARG;
+    for (int c = 0; c < h->ncases; ++c)
+        if (!h->initialized[c]) return LBM_ERR_STATE;
+    const int64_t bytes = lbm_checkpoint_size(h);
+    void* saved = nullptr;
+    if (cudaMallocAsync(&saved, (size_t)bytes, h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_OOM;
+    }
+    rc = checkpoint_copy(h, saved, true, true);
+    if (rc != LBM_OK) {
+        cudaFreeAsync(saved, h->stream);
+        return rc;
+    }
+    const int parity0 = h->parity;
+    const int64_t launches0 = h->launches;
+    std::vector<int64_t> steps0 = h->case_steps;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(h, LBM_ERR_CUDA);
+    float best = 1e30f;
+    int best_v = h->variant;
+    for (int v = 0; v < kNumVariants && rc == LBM_OK; ++v) {
+        h->variant = v;
+        rc = step_direct(h, 2);  // warm-up
+        cudaEventRecord(e0, h->stream);
+        if (rc == LBM_OK) rc = step_direct(h, 2 * reps);
+        cudaEventRecord(e1, h->stream);
+        if (rc == LBM_OK) rc = cuda_ok(h, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        if (rc == LBM_OK) cudaEventElapsedTime(&ms, e0, e1);
+        if (rc == LBM_OK && ms < best) {
+            best = ms;
+            best_v = v;
+        }
+        h->parity = parity0;
+        if (rc == LBM_OK) rc = checkpoint_copy(h, saved, false, true);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(saved, h->stream);
+    h->variant = best_v;
+    h->launches = launches0;
+    h->case_steps = steps0;
+    if (chosen) *chosen = best_v;
+    return rc;
+}
+
+int64_t lbm_kernel_launches(const lbm_handle* h) { return h ? h->launches : 0; }
+
+int lbm_destroy(lbm_handle* h) {
+    if (!h) return LBM_OK;
+    cudaSetDevice(h->device);
+    release(h);
+    delete h;
+    return LBM_OK;
+}
+
+const char* lbm_strerror(int status) {
+    switch (status) {
+        case LBM_OK: return "ok";
+        case LBM_ERR_INVALID_ARG: return "invalid argument";
+        case LBM_ERR_CUDA: return "CUDA runtime error";
+        case LBM_ERR_NONFINITE: return "non-finite value in phi, u or p";
+        case LBM_ERR_TIMEOUT: return "bounded device wait timed out";
+        case LBM_ERR_OOM: return "device out of memory";
+        case LBM_ERR_STATE: return "call out of order (case not initialised)";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,431 @@
+// lbm_device.cuh -- device-side arithmetic of one time step of the axisymmetric
+// Allen-Cahn phase-field MRT lattice Boltzmann method (Liang et al., arXiv
+// 1810.09299), written for sm_103a.
+//
+// The collision is done in moment space with the paper's closed forms:
+// Eq. 21-23 (phase field) and Eq. 36-37 (hydrodynamics), the transform M of
+// Sec. 2.2 unrolled into integer adds, M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6,
+// 1/12, 1/6, 1/12, 1/4, 1/4).  Everything a node needs is recomputed from the
+// populations each step: phi (Eq. 16) on a tile plus a two-node halo in shared
+// memory, then the stencils (Eq. 39-40), the local macroscopic quantities and
+// the collisions in registers, then the push streaming with the boundary rules.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace axilbm {
+
+// ---------------------------------------------------------------- lattice
+// D2Q9 of Eq. 12 with c_i = (c_z, c_r): 0 (0,0), 1 (1,0), 2 (0,1), 3 (-1,0),
+// 4 (0,-1), 5 (1,1), 6 (-1,1), 7 (-1,-1), 8 (1,-1).
+__host__ __device__ constexpr int cz_of(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cr_of(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr double w_of(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+__host__ __device__ constexpr int opp_of(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 5 + 2) % 4) + 5);
+}
+// reflection r -> -r: 2 <-> 4, 5 <-> 8, 6 <-> 7
+__host__ __device__ constexpr int rmir_of(int i) {
+    return i == 2 ? 4 : i == 4 ? 2 : i == 5 ? 8 : i == 8 ? 5 : i == 6 ? 7 : i == 7 ? 6 : i;
+}
+
+// ---------------------------------------------------------------- per-case data
+// Per-case constants in the arithmetic precision of the kernel (converted once
+// on the host: the FP32 kernels never touch the FP64 pipe for parameters).
+template <typename Real>
+struct CaseReal {
+    Real rho_l, rho_g, nu_l, nu_g, grav_z, n_eps;
+    Real beta, kappa, inv_W, mob;
+    Real sf[9];   // phase-field rates, derived entries already resolved (Eq. 18)
+    Real sg[9];   // hydrodynamic rates; entries flagged in sg_local are 1/tau_g(x)
+};
+
+struct CaseDev {
+    int32_t nr, nz, pitch, zper;
+    int32_t p_coupling;
+    uint32_t sg_local;  // bit i set: sg[i] = 1/tau_g(x) from the local viscosity (Eq. 34)
+    int64_t off;        // element offset of the case inside every plane of the pooled arrays
+    CaseReal<double> pd;
+    CaseReal<float> pf;
+};
+
+template <typename Real>
+__device__ __forceinline__ const CaseReal<Real>& case_params(const CaseDev& C);
+template <>
+__device__ __forceinline__ const CaseReal<double>& case_params<double>(const CaseDev& C) { return C.pd; }
+template <>
+__device__ __forceinline__ const CaseReal<float>& case_params<float>(const CaseDev& C) { return C.pf; }
+
+// One tile of one case: (case, k0, j0)
+struct TileDev {
+    int32_t c, k0, j0, pad;
+};
+
+// ---------------------------------------------------------------- storage codecs
+// Populations are stored as PT (f_1..8, g_0..8) and F0T (f_0).  wr = w_i * r of
+// the node the value is stored at (known to writer and reader), inv_wr = 1/wr.
+//
+// In the FP32 and 16-bit codecs f_0 is the node's mass ledger, a double-float
+// pair (hi, lo): each step it is rewritten as (sum of the node's incoming
+// populations) minus (its outgoing f_1..8), accumulated with error-free
+// TwoSum steps (Knuth), so the sum of all populations is conserved to ~2^-48
+// relative although the collision runs in FP32 and f_1..8 are rounded.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ void ff_add(FF& a, float x) {
+    const float s = a.hi + x;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (x - bb);
+    a.hi = s;
+    a.lo += e;
+}
+__device__ __forceinline__ FF ff_norm(FF a) {
+    const float h = a.hi + a.lo;
+    return FF{h, a.lo - (h - a.hi)};
+}
+
+struct CodecF64 {
+    using Real = double;
+    using PT = double;
+    using F0T = double;
+    static constexpr bool kLedger = false;
+    __device__ static Real dec_f(PT v, Real) { return v; }
+    __device__ static PT enc_f(Real v, Real, Real) { return v; }
+    __device__ static Real dec_g(PT v, Real) { return v; }
+    __device__ static PT enc_g(Real v, Real, Real) { return v; }
+};
+
+struct CodecF32 {
+    using Real = float;
+    using PT = float;
+    using F0T = float2;
+    static constexpr bool kLedger = true;
+    __device__ static Real dec_f(PT v, Real) { return v; }
+    __device__ static PT enc_f(Real v, Real, Real) { return v; }
+    __device__ static Real dec_g(PT v, Real) { return v; }
+    __device__ static PT enc_g(Real v, Real, Real) { return v; }
+};
+
+// 16-bit deviation storage: f_i / (w_i r) - 1/2 (phi-like, centred) and
+// g_i / (w_i r) * scale (rest state g = 0; the scale keeps typical values
+// out of the FP16 subnormal range).
+struct CodecH16 {
+    using Real = float;
+    using PT = __half;
+    using F0T = float2;
+    static constexpr bool kLedger = true;
+    static constexpr float kGScale = 256.0f;
+    __device__ static Real dec_f(PT v, Real wr) { return (__half2float(v) + 0.5f) * wr; }
+    __device__ static PT enc_f(Real v, Real, Real inv_wr) { return __float2half_rn(v * inv_wr - 0.5f); }
+    __device__ static Real dec_g(PT v, Real wr) { return __half2float(v) * (wr * (1.0f / kGScale)); }
+    __device__ static PT enc_g(Real v, Real, Real inv_wr) { return __float2half_rn(v * inv_wr * kGScale); }
+};
+
+struct CodecB16 {
+    using Real = float;
+    using PT = __nv_bfloat16;
+    using F0T = float2;
+    static constexpr bool kLedger = true;
+    __device__ static Real dec_f(PT v, Real wr) { return (__bfloat162float(v) + 0.5f) * wr; }
+    __device__ static PT enc_f(Real v, Real, Real inv_wr) { return __float2bfloat16_rn(v * inv_wr - 0.5f); }
+    __device__ static Real dec_g(PT v, Real wr) { return __bfloat162float(v) * wr; }
+    __device__ static PT enc_g(Real v, Real, Real inv_wr) { return __float2bfloat16_rn(v * inv_wr); }
+};
+
+// f_0 as a value of the arithmetic type.
+__device__ __forceinline__ double f0_value(double v) { return v; }
+__device__ __forceinline__ float f0_value(float2 v) { return v.x + v.y; }
+
+template <class Codec>
+struct StateDev {
+    using PT = typename Codec::PT;
+    using F0T = typename Codec::F0T;
+    using Real = typename Codec::Real;
+    const F0T* f0_in;
+    const PT* fq_in;  // planes 0..7 hold f_1..f_8
+    const PT* g_in;   // planes 0..8 hold g_0..g_8
+    F0T* f0_out;
+    PT* fq_out;
+    PT* g_out;
+    Real* chi_z;  // chi^{n-1}, updated in place to chi^n
+    Real* chi_r;
+    Real* p_prev;  // p^{n-1}, updated in place (lagged coupling only)
+    int64_t total;  // elements per plane of the pooled arrays
+};
+
+// ---------------------------------------------------------------- ghost rules
+// Sec. 2.3: mirror about the axis (r = 0 lies between j = -1 and j = 0), mirror
+// about the halfway wall planes, periodic wrap in z.  The result is clamped
+// into the domain so that halo cells beyond the two-node ghost ring (ragged
+// tiles) stay in bounds; they are never used by a real node.
+__device__ __forceinline__ int ghost_r(int j, int nr) {
+    if (j < 0) j = -1 - j;
+    if (j >= nr) j = 2 * nr - 1 - j;
+    return min(max(j, 0), nr - 1);
+}
+__device__ __forceinline__ int ghost_z(int k, int nz, int zper) {
+    if (zper) {
+        k %= nz;
+        if (k < 0) k += nz;
+        return k;
+    }
+    if (k < 0) k = -1 - k;
+    if (k >= nz) k = 2 * nz - 1 - k;
+    return min(max(k, 0), nz - 1);
+}
+
+// phi at an in-domain node from its stored populations (Eq. 16).
+template <class Codec>
+__device__ __forceinline__ typename Codec::Real node_phi(const StateDev<Codec>& S, int64_t node,
+                                                          typename Codec::Real r,
+                                                          typename Codec::Real inv_r) {
+    using Real = typename Codec::Real;
+    Real s = (Real)f0_value(S.f0_in[node]);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        s += Codec::dec_f(S.fq_in[(int64_t)(i - 1) * S.total + node], (Real)w_of(i) * r);
+    }
+    return s * inv_r;
+}
+
+// ---------------------------------------------------------------- arithmetic helpers
+// FP32: hardware reciprocal / division (at most 2 ulp, far below the FP32
+// rounding the method accumulates anyway); FP64: IEEE division.
+__device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_(double a, double b) { return a / b; }
+
+// ---------------------------------------------------------------- macroscopic part
+template <typename Real>
+struct Macro {
+    Real r, inv_r, phi, rho, nu;
+    Real gz, gr, lap;
+    Real uz, ur, p, pstar;
+    Real Fz, Fr;
+    Real nzn, nrn, lam;
+    Real sg[9];
+    Real mg[9];  // M g (hydrodynamic moments before collision)
+};
+
+// Stencils (Eq. 39, Eq. 40) from the shared phi window centred on (cz0, cr0).
+template <typename Real, int LD>
+__device__ __forceinline__ void stencil(const Real* sphi, int a, int b, Real& gz, Real& gr, Real& lap) {
+    const Real c0 = sphi[a * LD + b];
+    Real sz = 0, sr = 0, sl = 0;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const Real x1 = sphi[(a + cz_of(i)) * LD + (b + cr_of(i))];
+        const Real x2 = sphi[(a + 2 * cz_of(i)) * LD + (b + 2 * cr_of(i))];
+        const Real w = (Real)w_of(i);
+        const Real d = (Real)8 * x1 - x2;
+        if (cz_of(i) != 0) sz += (Real)cz_of(i) * w * d;
+        if (cr_of(i) != 0) sr += (Real)cr_of(i) * w * d;
+        sl += w * ((Real)16 * x1 - x2 - (Real)15 * c0);
+    }
+    // divide by 6 cs^2 = 2
+    gz = sz * (Real)0.5;
+    gr = sr * (Real)0.5;
+    lap = sl * (Real)0.5;
+}
+
+// M g for the nine hydrodynamic populations (rows of M in Sec. 2.2).
+template <typename Real>
+__device__ __forceinline__ void moments(const Real* x, Real* m) {
+    const Real a14 = x[1] + x[2] + x[3] + x[4];
+    const Real a58 = x[5] + x[6] + x[7] + x[8];
+    m[0] = x[0] + a14 + a58;
+    m[1] = (Real)-4 * x[0] - a14 + (Real)2 * a58;
+    m[2] = (Real)4 * x[0] - (Real)2 * a14 + a58;
+    const Real d57 = x[5] - x[7], d68 = x[6] - x[8];
+    m[3] = x[1] - x[3] + d57 - d68;
+    m[4] = (Real)-2 * (x[1] - x[3]) + d57 - d68;
+    m[5] = x[2] - x[4] + d57 + d68;
+    m[6] = (Real)-2 * (x[2] - x[4]) + d57 + d68;
+    m[7] = x[1] - x[2] + x[3] - x[4];
+    m[8] = x[5] - x[6] + x[7] - x[8];
+}
+
+// x = M^-1 m with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
+template <typename Real>
+__device__ __forceinline__ void inverse_moments(const Real* m, Real* x) {
+    const Real a0 = m[0] * (Real)(1.0 / 9.0);
+    const Real a1 = m[1] * (Real)(1.0 / 36.0);
+    const Real a2 = m[2] * (Real)(1.0 / 36.0);
+    const Real a3 = m[3] * (Real)(1.0 / 6.0);
+    const Real a4 = m[4] * (Real)(1.0 / 12.0);
+    const Real a5 = m[5] * (Real)(1.0 / 6.0);
+    const Real a6 = m[6] * (Real)(1.0 / 12.0);
+    const Real a7 = m[7] * (Real)0.25;
+    const Real a8 = m[8] * (Real)0.25;
+    const Real e = a0 - a1 - (Real)2 * a2;   // axis directions, isotropic part
+    const Real d = a0 + (Real)2 * a1 + a2;   // diagonal directions, isotropic part
+    const Real jz = a3 - (Real)2 * a4, jr = a5 - (Real)2 * a6;
+    const Real qz = a3 + a4, qr = a5 + a6;
+    x[0] = a0 - (Real)4 * a1 + (Real)4 * a2;
+    x[1] = e + jz + a7;
+    x[2] = e + jr - a7;
+    x[3] = e - jz + a7;
+    x[4] = e - jr - a7;
+    x[5] = d + qz + qr + a8;
+    x[6] = d - qz + qr - a8;
+    x[7] = d - qz - qr + a8;
+    x[8] = d + qz - qr - a8;
+}
+
+// Everything before the collisions for node (k, j) of case C, from the
+// shared phi window (centred on (a, b)) and the node's decoded g.
+template <typename Real, int LD>
+__device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, int a, int b, int j, const Real* g,
+                                            Real p_prev, Macro<Real>& m) {
+    const CaseReal<Real>& P = case_params<Real>(C);
+    m.r = (Real)j + (Real)0.5;
+    m.inv_r = rcp_(m.r);
+    m.phi = sphi[a * LD + b];
+    stencil<Real, LD>(sphi, a, b, m.gz, m.gr, m.lap);
+    const Real rho_l = P.rho_l, rho_g = P.rho_g;
+    m.rho = m.phi * rho_l + ((Real)1 - m.phi) * rho_g;                    // Eq. 17
+    m.nu = m.phi * P.nu_l + ((Real)1 - m.phi) * P.nu_g;                  // Eq. 35
+    const Real sgv = rcp_((Real)3 * m.nu + (Real)0.5);                    // Eq. 34
+#pragma unroll
+    for (int i = 0; i < 9; ++i) m.sg[i] = ((C.sg_local >> i) & 1u) ? sgv : P.sg[i];
+    // Eq. 4 and mu~ = mu - k d_r phi / r
+    const Real kap = P.kappa;
+    const Real mu = (Real)4 * P.beta * m.phi * (m.phi - (Real)1) * (m.phi - (Real)0.5) - kap * m.lap;
+    const Real mut = mu - kap * m.gr * m.inv_r;
+    const Real Fsz = mut * m.gz, Fsr = mut * m.gr;
+    const Real Gz = (m.rho - rho_l) * P.grav_z;
+    // interface normal and lambda (Eq. 2)
+    const Real ign = rcp_(sqrt(m.gz * m.gz + m.gr * m.gr) + P.n_eps);
+    m.nzn = m.gz * ign;
+    m.nrn = m.gr * ign;
+    m.lam = (Real)4 * m.phi * ((Real)1 - m.phi) * P.inv_W;
+    // hydrodynamic moments
+    moments<Real>(g, m.mg);
+    const Real Jz = m.mg[3], Jr = m.mg[5], S0 = m.mg[0] - g[0];
+    const Real drho = rho_l - rho_g;
+    const Real dzrho = drho * m.gz, drrho = drho * m.gr;
+    const Real s1 = m.sg[1], s2 = m.sg[2];
+    const Real sp = div_(s1 + s2 - s1 * s2, (Real)2 * s1 * s2);
+    const Real r = m.r;
+    m.uz = div_(Jz + (Real)0.5 * r * (Fsz + Gz), r * m.rho);              // Eq. 32 (z)
+    const Real iDr = rcp_(r * m.rho + m.nu * m.rho * m.inv_r);
+    if (C.p_coupling == 1) {
+        m.pstar = p_prev;
+        m.ur = (Jr + (Real)0.5 * (r * Fsr + m.pstar)) * iDr;                // Eq. 32 (r)
+        m.p = (Real)0.6 * (S0 * m.inv_r + (Real)0.5 * (m.uz * dzrho + m.ur * drrho) -
+                           (Real)(2.0 / 3.0) * m.rho * (m.uz * m.uz + m.ur * m.ur) -
+                           sp * (Real)(4.0 / 9.0) * m.rho * m.ur * m.inv_r); // Eq. 33
+    } else {
+        // Eq. 32 (r) and Eq. 33 together: u_r = a + b p, p = A0 + A1 u_r - A2 u_r^2
+        const Real ca = (Jr + (Real)0.5 * r * Fsr) * iDr;
+        const Real cb = (Real)0.5 * iDr;
+        const Real A0 = (Real)0.6 * (S0 * m.inv_r + (Real)0.5 * m.uz * dzrho - (Real)(2.0 / 3.0) * m.rho * m.uz * m.uz);
+        const Real A1 = (Real)0.6 * ((Real)0.5 * drrho - sp * (Real)(4.0 / 9.0) * m.rho * m.inv_r);
+        const Real A2 = (Real)0.4 * m.rho;
+        const Real qa = A2 * cb * cb;
+        const Real qb = (Real)1 - A1 * cb + (Real)2 * A2 * ca * cb;
+        const Real qc = -(A0 + A1 * ca - A2 * ca * ca);
+        const Real disc = qb * qb - (Real)4 * qa * qc;
+        m.p = (disc >= (Real)0) ? div_((Real)-2 * qc, qb + sqrt(disc)) : div_(-qc, qb);
+        m.pstar = m.p;
+        m.ur = ca + cb * m.p;
+    }
+    // Eq. 30
+    m.Fz = r * (Fsz + Gz);
+    m.Fr = r * Fsr + m.pstar - (Real)2 * m.rho * m.nu * m.ur * m.inv_r;
+}
+
+// ---------------------------------------------------------------- collisions
+// Phase field (Eq. 19 in moment space with Eq. 21-23).  chi = (r phi u_z,
+// r phi u_r + M phi); the time derivative of Eq. 38 uses chi^{n-1}.
+template <typename Real>
+__device__ __forceinline__ void collide_f(const CaseDev& C, const Macro<Real>& m, const Real* f, Real chi_z_prev,
+                                          Real chi_r_prev, Real& chi_z, Real& chi_r, Real* fpost) {
+    const CaseReal<Real>& P = case_params<Real>(C);
+    Real mf[9];
+    moments<Real>(f, mf);
+    const Real rphi = mf[0];  // = r phi exactly (phi is sum f / r)
+    chi_z = m.r * m.phi * m.uz;
+    chi_r = m.r * m.phi * m.ur + P.mob * m.phi;
+    const Real mR1 = (chi_z - chi_z_prev) + m.r * m.nzn * m.lam * (Real)(1.0 / 3.0);
+    const Real mR2 = (chi_r - chi_r_prev) + m.r * m.nrn * m.lam * (Real)(1.0 / 3.0);
+    const Real meq[9] = {rphi, (Real)-2 * rphi, rphi, chi_z, -chi_z, chi_r, -chi_r, (Real)0, (Real)0};
+    const Real mR[9] = {(Real)0, (Real)0, (Real)0, mR1, -mR1, mR2, -mR2, (Real)0, (Real)0};
+    Real mp[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const Real s = P.sf[k];
+        mp[k] = mf[k] - s * (mf[k] - meq[k]) + ((Real)1 - (Real)0.5 * s) * mR[k];
+    }
+    inverse_moments<Real>(mp, fpost);
+}
+
+// Hydrodynamics (Eq. 24 in moment space with Eq. 36-37).
+template <typename Real>
+__device__ __forceinline__ void collide_g(const CaseDev& C, const Macro<Real>& m, Real* gpost) {
+    const CaseReal<Real>& P = case_params<Real>(C);
+    const Real r = m.r, rho = m.rho, uz = m.uz, ur = m.ur, p = m.p;
+    const Real u2 = uz * uz + ur * ur;
+    const Real drho = P.rho_l - P.rho_g;
+    const Real dz_rr = r * drho * m.gz;          // d_z (r rho)
+    const Real dr_rr = rho + r * drho * m.gr;    // d_r (r rho)
+    const Real udr = uz * dz_rr + ur * dr_rr;
+    const Real meq[9] = {(Real)0,
+                         r * (Real)3 * ((Real)2 * p + rho * u2),
+                         -r * (Real)3 * ((Real)3 * p + rho * u2),
+                         r * rho * uz, -r * rho * uz,
+                         r * rho * ur, -r * rho * ur,
+                         r * rho * (uz * uz - ur * ur),
+                         r * rho * ur * uz};
+    const Real MT[9] = {udr - rho * ur,  // = r u . grad rho
+                        (Real)2 * rho * ur,
+                        -udr - rho * ur,
+                        m.Fz, -m.Fz, m.Fr, -m.Fr,
+                        (Real)(2.0 / 3.0) * (uz * dz_rr - ur * dr_rr),
+                        (Real)(1.0 / 3.0) * (uz * dr_rr + ur * dz_rr)};
+    Real mp[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const Real s = m.sg[k];
+        mp[k] = m.mg[k] - s * (m.mg[k] - meq[k]) + ((Real)1 - (Real)0.5 * s) * MT[k];
+    }
+    inverse_moments<Real>(mp, gpost);
+}
+
+// ---------------------------------------------------------------- streaming
+// Push f+_i(k, j) along c_i (Eq. 20).  A link that leaves through a wall (the
+// z-walls when not periodic, the wall r = nr, and any corner) is bounced back
+// to its own node as direction opp(i); a link that leaves through the axis
+// alone enters (k + c_z, 0) as the r-mirrored direction.
+struct Dest {
+    int k, j, dir;
+};
+template <int I>
+__device__ __forceinline__ Dest destination(int k, int j, int nr, int nz, int zper) {
+    int kt = k + cz_of(I);
+    const int jt = j + cr_of(I);
+    bool zout = false;
+    if (cz_of(I) != 0) {
+        if (zper) {
+            kt = kt < 0 ? kt + nz : (kt >= nz ? kt - nz : kt);
+        } else {
+            zout = (kt < 0) || (kt >= nz);
+        }
+    }
+    const bool rwall = (cr_of(I) > 0) && (jt >= nr);
+    if (zout || rwall) return Dest{k, j, opp_of(I)};
+    if (cr_of(I) < 0 && jt < 0) return Dest{kt, 0, rmir_of(I)};
+    return Dest{kt, jt, I};
+}
+
+}  // namespace axilbm

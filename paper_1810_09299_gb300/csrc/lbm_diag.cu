@@ -1,0 +1,221 @@
+// lbm_diag.cu -- FP64 diagnostics of one case (compensated, deterministic
+// reductions) and the initial phase-field shapes of the paper's tests (Sec. 3).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "lbm_internal.h"
+
+namespace axilbm {
+
+namespace {
+
+constexpr int kDiagBlocks = 304;   // 2 x 152 SMs; fixed so the summation order is fixed
+constexpr int kDiagThreads = 256;
+
+// Neumaier compensated accumulation.
+struct KSum {
+    double s, c;
+    __device__ void add(double x) {
+        const double t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    __device__ void merge(const KSum& o) {
+        add(o.s);
+        c += o.c;
+    }
+    __device__ double value() const { return s + c; }
+};
+
+// Quantities: 0 mass, 1 kinetic, 2 z-moment, 3 p in liquid, 4 weight in liquid,
+// 5 p in gas, 6 weight in gas (sums); 7 umax, 8 phi_min, 9 phi_max (extrema);
+// 10 non-finite count (sum).
+__global__ void __launch_bounds__(kDiagThreads) diag_partial_kernel(const double* __restrict__ F, int nz, int nr,
+                                                                    double* __restrict__ partials) {
+    const int64_t n = (int64_t)nz * nr;
+    KSum acc[7] = {};
+    double umax = 0.0, pmin = INFINITY, pmax = -INFINITY, bad = 0.0;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(o / nr), j = (int)(o - (int64_t)k * nr);
+        const double r = j + 0.5, z = k + 0.5;
+        const double phi = F[o], rho = F[n + o], uz = F[2 * n + o], ur = F[3 * n + o], p = F[4 * n + o];
+        if (!isfinite(phi) || !isfinite(uz) || !isfinite(ur) || !isfinite(p)) {
+            bad += 1.0;
+            continue;
+        }
+        const double uu = uz * uz + ur * ur;
+        acc[0].add(r * phi);
+        acc[1].add(0.5 * r * rho * uu);
+        acc[2].add(r * z * phi);
+        if (phi > 0.99) {
+            acc[3].add(r * p);
+            acc[4].add(r);
+        }
+        if (phi < 0.01) {
+            acc[5].add(r * p);
+            acc[6].add(r);
+        }
+        umax = fmax(umax, sqrt(uu));
+        pmin = fmin(pmin, phi);
+        pmax = fmax(pmax, phi);
+    }
+    __shared__ double sh[kDiagThreads][2 * 7 + 4];
+    for (int q = 0; q < 7; ++q) {
+        sh[threadIdx.x][2 * q] = acc[q].s;
+        sh[threadIdx.x][2 * q + 1] = acc[q].c;
+    }
+    sh[threadIdx.x][14] = umax;
+    sh[threadIdx.x][15] = pmin;
+    sh[threadIdx.x][16] = pmax;
+    sh[threadIdx.x][17] = bad;
+    __syncthreads();
+    for (int stride = kDiagThreads / 2; stride > 0; stride >>= 1) {
+        if (threadIdx.x < stride) {
+            double* a = sh[threadIdx.x];
+            const double* b = sh[threadIdx.x + stride];
+            for (int q = 0; q < 7; ++q) {
+                KSum x{a[2 * q], a[2 * q + 1]};
+                x.merge(KSum{b[2 * q], b[2 * q + 1]});
+                a[2 * q] = x.s;
+                a[2 * q + 1] = x.c;
+            }
+            a[14] = fmax(a[14], b[14]);
+            a[15] = fmin(a[15], b[15]);
+            a[16] = fmax(a[16], b[16]);
+            a[17] += b[17];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 18; ++q) partials[blockIdx.x * 18 + q] = sh[0][q];
+    }
+}
+
+// Final combination (one thread, fixed order) and the interface lengths.
+__global__ void diag_final_kernel(const double* __restrict__ F, int nz, int nr, int zper, double step,
+                                  const double* __restrict__ partials, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    KSum acc[7] = {};
+    double umax = 0.0, pmin = INFINITY, pmax = -INFINITY, bad = 0.0;
+    for (int b = 0; b < kDiagBlocks; ++b) {
+        const double* p = partials + b * 18;
+        for (int q = 0; q < 7; ++q) acc[q].merge(KSum{p[2 * q], p[2 * q + 1]});
+        umax = fmax(umax, p[14]);
+        pmin = fmin(pmin, p[15]);
+        pmax = fmax(pmax, p[16]);
+        bad += p[17];
+    }
+    const double mass = acc[0].value();
+    const double zc = acc[2].value() / mass;
+    const double win = acc[4].value(), wout = acc[6].value();
+    const double dp = (win > 0 ? acc[3].value() / win : 0.0) - (wout > 0 ? acc[5].value() / wout : 0.0);
+    // half-length of the phi > 1/2 set on the axis row (linear crossings)
+    double len = 0.0;
+    for (int k = 0; k < nz; ++k) {
+        const double a = F[(int64_t)k * nr] - 0.5;
+        int kn = k + 1;
+        if (kn >= nz) {
+            if (!zper) {
+                if (a > 0) len += 0.5;
+                break;
+            }
+            kn = 0;
+        }
+        const double b = F[(int64_t)kn * nr] - 0.5;
+        if (a > 0 && b > 0) len += 1.0;
+        else if (a > 0 && b <= 0) len += a / (a - b);
+        else if (a <= 0 && b > 0) len += b / (b - a);
+    }
+    if (!zper && F[0] - 0.5 > 0) len += 0.5;
+    // radial crossing on the row nearest the centroid
+    int kc = (int)floor(zc);
+    kc = kc < 0 ? 0 : (kc >= nz ? nz - 1 : kc);
+    double rc = 0.0;
+    for (int j = 0; j + 1 < nr; ++j) {
+        const double a = F[(int64_t)kc * nr + j] - 0.5, b = F[(int64_t)kc * nr + j + 1] - 0.5;
+        if (a > 0 && b <= 0) {
+            rc = (j + 0.5) + a / (a - b);
+            break;
+        }
+    }
+    out[0] = step;
+    out[1] = mass;
+    out[2] = acc[1].value();
+    out[3] = zc;
+    out[4] = dp;
+    out[5] = umax;
+    out[6] = pmin;
+    out[7] = pmax;
+    out[8] = 0.5 * len;
+    out[9] = rc;
+    out[10] = bad;
+}
+
+// ---------------------------------------------------------------- shapes
+struct ShapeArgs {
+    double a[8];
+};
+
+__global__ void shape_kernel(int shape, ShapeArgs A, int nz, int nr, double* __restrict__ phi) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (j >= nr || k >= nz) return;
+    const double z = k + 0.5, r = j + 0.5;
+    double v = 0.0;
+    switch (shape) {
+        case 0: {  // flat: {z_i, W, axis}
+            const double x = (A.a[2] == 0.0) ? z : r;
+            v = 0.5 + 0.5 * tanh(2.0 * (A.a[0] - x) / A.a[1]);
+            break;
+        }
+        case 1:
+        case 5: {  // sphere / bubble: {z_c, R, W}
+            const double d = sqrt((z - A.a[0]) * (z - A.a[0]) + r * r);
+            v = 0.5 + 0.5 * tanh(2.0 * (A.a[1] - d) / A.a[2]);
+            if (shape == 5) v = 1.0 - v;
+            break;
+        }
+        case 2: {  // ellipsoid: {z_c, R_z, R_r, W}
+            const double Re = cbrt(A.a[2] * A.a[2] * A.a[1]);
+            const double q = sqrt((z - A.a[0]) * (z - A.a[0]) / (A.a[1] * A.a[1]) + r * r / (A.a[2] * A.a[2]));
+            v = 0.5 + 0.5 * tanh(2.0 * Re * (1.0 - q) / A.a[3]);
+            break;
+        }
+        case 3: {  // P2 drop: {z_c, R0, eps, W}
+            const double d = sqrt((z - A.a[0]) * (z - A.a[0]) + r * r);
+            const double c = (z - A.a[0]) / fmax(d, 1e-300);
+            const double Rs = A.a[1] * (1.0 + A.a[2] * 0.5 * (3.0 * c * c - 1.0));
+            v = 0.5 + 0.5 * tanh(2.0 * (Rs - d) / A.a[3]);
+            break;
+        }
+        case 4: {  // thread: {R, amp, lambda, theta, W}
+            const double d = A.a[1] * cos(2.0 * M_PI * z / A.a[2] + A.a[3]);
+            v = 0.5 + 0.5 * tanh(2.0 * (A.a[0] + d - r) / A.a[4]);
+            break;
+        }
+        default:
+            v = 0.0;
+    }
+    phi[(int64_t)k * nr + j] = v;
+}
+
+}  // namespace
+
+int diag_partials_size() { return kDiagBlocks * 18; }
+
+cudaError_t launch_diag(const double* fields, int nz, int nr, int zper, double step, double* partials, double* out,
+                        cudaStream_t st) {
+    diag_partial_kernel<<<kDiagBlocks, kDiagThreads, 0, st>>>(fields, nz, nr, partials);
+    diag_final_kernel<<<1, 32, 0, st>>>(fields, nz, nr, zper, step, partials, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shape(int shape, const double* args, int nargs, int nz, int nr, double* phi0, cudaStream_t st) {
+    ShapeArgs A{};
+    for (int i = 0; i < nargs && i < 8; ++i) A.a[i] = args[i];
+    dim3 grid((nr + 127) / 128, nz);
+    shape_kernel<<<grid, 128, 0, st>>>(shape, A, nz, nr, phi0);
+    return cudaGetLastError();
+}
+
+}  // namespace axilbm

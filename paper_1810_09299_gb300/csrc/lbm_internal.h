@@ -1,0 +1,60 @@
+// lbm_internal.h -- host-side declarations shared by the C ABI and the
+// per-precision kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace axilbm {
+
+struct CaseDev;
+struct TileDev;
+
+// Device buffers of a handle.  Every array is a set of planes of `total`
+// elements; case c occupies elements [off_c, off_c + nz_c * pitch_c) of each
+// plane.  f0 holds f_0 (1 plane), fq holds f_1..f_8 (8 planes), g holds g_0..g_8
+// (9 planes); index [parity] selects the A/B copy read by the next step.
+struct DeviceState {
+    void* f0[2];
+    void* fq[2];
+    void* g[2];
+    void* chi_z;
+    void* chi_r;
+    void* p_prev;
+    void* cases;  // CaseDev[ncases] on the device
+    int64_t total;
+};
+
+#define AXILBM_DECLARE(NAME)                                                                                       \
+    cudaError_t launch_step_##NAME(const DeviceState& D, int parity, int variant, const TileDev* tiles, int ntiles, \
+                                   cudaStream_t st);                                                               \
+    cudaError_t launch_fields_##NAME(const DeviceState& D, int parity, const TileDev* tiles, int ntiles,            \
+                                     double* out, cudaStream_t st);                                                \
+    cudaError_t launch_init_##NAME(const DeviceState& D, int parity, const CaseDev& C, const double* phi0,          \
+                                   cudaStream_t st);                                                               \
+    cudaError_t launch_get_state_##NAME(const DeviceState& D, int parity, const CaseDev& C, double* f, double* g,   \
+                                        double* aux, cudaStream_t st);                                             \
+    cudaError_t launch_set_state_##NAME(const DeviceState& D, int parity, const CaseDev& C, const double* f,        \
+                                        const double* g, const double* aux, cudaStream_t st);
+
+AXILBM_DECLARE(f64)
+AXILBM_DECLARE(f32)
+AXILBM_DECLARE(h16)
+AXILBM_DECLARE(b16)
+#undef AXILBM_DECLARE
+
+constexpr int kNumVariants = 3;
+// tile height along z of each step-kernel variant (tile width is one warp along r)
+constexpr int kVariantTZ[kNumVariants] = {8, 16, 4};
+
+// Diagnostics (lbm_diag.cu): reduce dense FP64 fields of one case into a
+// 11-double record; `partials` is scratch of at least diag_partials_size()
+// doubles.  Deterministic (fixed block count and order).
+int diag_partials_size();
+cudaError_t launch_diag(const double* fields, int nz, int nr, int zper, double step, double* partials,
+                        double* out, cudaStream_t st);
+
+// Initial shapes (lbm_diag.cu): phi0 [nz][nr] on the device.
+cudaError_t launch_shape(int shape, const double* args, int nargs, int nz, int nr, double* phi0, cudaStream_t st);
+
+}  // namespace axilbm

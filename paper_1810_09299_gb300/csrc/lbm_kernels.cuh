@@ -1,0 +1,412 @@
+// lbm_kernels.cuh -- kernel templates of the step, the field recovery, the
+// initial condition and the state transfer.  Each precision's .cu file
+// includes this header and instantiates the launchers for its codec.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace axilbm {
+
+constexpr int kTR = 32;  // tile width along r = one warp
+
+// phi at window position (a, b) of tile t through the ghost rules.
+template <class Codec>
+__device__ __forceinline__ typename Codec::Real window_phi(const CaseDev& C, const StateDev<Codec>& S,
+                                                            const TileDev& t, int a, int b) {
+    using Real = typename Codec::Real;
+    const int k = ghost_z(t.k0 - 2 + a, C.nz, C.zper);
+    const int j = ghost_r(t.j0 - 2 + b, C.nr);
+    const Real r = (Real)j + (Real)0.5;
+    return node_phi<Codec>(S, C.off + (int64_t)k * C.pitch + j, r, rcp_(r));
+}
+
+// Minimum resident CTAs per SM requested from the register allocator.
+template <class Codec, int BZ>
+constexpr int step_min_blocks() {
+    return sizeof(typename Codec::Real) == 8 ? 1 : (BZ >= 16 ? 1 : (BZ >= 8 ? 3 : 6));
+}
+
+// One time step for every node of every tile in `tiles`: one CTA per tile of
+// BZ rows (z) x 32 columns (r), one node per thread.  Each thread first issues
+// the loads of its own node; the node's phi goes to the shared window straight
+// from those registers and only the two-node ring around the tile is
+// recomputed from neighbours' populations.
+template <class Codec, int BZ>
+__global__ void __launch_bounds__(kTR * BZ, (step_min_blocks<Codec, BZ>()))
+step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles, StateDev<Codec> S) {
+    using Real = typename Codec::Real;
+    using PT = typename Codec::PT;
+    using F0T = typename Codec::F0T;
+    constexpr int TZ = BZ;
+    constexpr int LD = kTR + 4;
+    constexpr int NRING = 4 * LD + 4 * TZ;
+    __shared__ Real sphi[(TZ + 4) * LD];
+    const TileDev t = tiles[blockIdx.x];
+    const CaseDev& C = cases[t.c];
+    const int j = t.j0 + threadIdx.x;
+    const int k = t.k0 + threadIdx.y;
+    const bool inside = (j < C.nr) && (k < C.nz);
+    const int64_t node = C.off + (int64_t)k * C.pitch + j;
+
+    // 1. own-node loads, issued before anything waits on memory
+    F0T f0raw{};
+    PT fraw[8], graw[9];
+    Real chz_prev = (Real)0, chr_prev = (Real)0, p_prev = (Real)0;
+    if (inside) {
+        f0raw = S.f0_in[node];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) fraw[i] = S.fq_in[(int64_t)i * S.total + node];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) graw[i] = S.g_in[(int64_t)i * S.total + node];
+        chz_prev = S.chi_z[node];
+        chr_prev = S.chi_r[node];
+        if (C.p_coupling == 1) p_prev = S.p_prev[node];
+    }
+    // 2. the ring of the phi window (two rows above and below, two columns
+    //    left and right of the tile)
+    for (int q = threadIdx.y * kTR + threadIdx.x; q < NRING; q += kTR * BZ) {
+        int a, b;
+        if (q < 2 * LD) {
+            a = q / LD;
+            b = q - a * LD;
+        } else if (q < 4 * LD) {
+            const int q2 = q - 2 * LD;
+            a = TZ + 2 + q2 / LD;
+            b = q2 - (q2 / LD) * LD;
+        } else {
+            const int q3 = q - 4 * LD;
+            const int c = q3 / TZ;
+            a = 2 + (q3 - c * TZ);
+            b = c < 2 ? c : kTR + c;
+        }
+        sphi[a * LD + b] = window_phi<Codec>(C, S, t, a, b);
+    }
+    // 3. the node's own phi (Eq. 16); window cells outside the domain take the ghost rule
+    const Real r = (Real)j + (Real)0.5;
+    Real f[9];
+    if (inside) {
+        f[0] = (Real)f0_value(f0raw);
+        Real sum = f[0];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            f[i] = Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
+            sum += f[i];
+        }
+        sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = sum * rcp_(r);
+    } else {
+        sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = window_phi<Codec>(C, S, t, threadIdx.y + 2, threadIdx.x + 2);
+    }
+    __syncthreads();
+    if (!inside) return;
+
+    // 4. macroscopic recovery and the two collisions
+    Real g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = Codec::dec_g(graw[i], (Real)w_of(i) * r);
+    Macro<Real> m;
+    node_macros<Real, LD>(C, sphi, threadIdx.y + 2, threadIdx.x + 2, j, g, p_prev, m);
+    FF ledger{0.0f, 0.0f};
+    if constexpr (Codec::kLedger) {
+        ledger = FF{((const float2&)f0raw).x, ((const float2&)f0raw).y};
+#pragma unroll
+        for (int i = 1; i < 9; ++i) ff_add(ledger, (float)f[i]);  // incoming total, exact
+    }
+    Real fp[9], chz, chr;
+    collide_f<Real>(C, m, f, chz_prev, chr_prev, chz, chr, fp);
+    S.chi_z[node] = chz;
+    S.chi_r[node] = chr;
+    if (C.p_coupling == 1) S.p_prev[node] = m.p;
+    Real gp[9];
+    collide_g<Real>(C, m, gp);
+
+    // 5. streaming (Eq. 20) with the boundary rules; rows j-1, j, j+1 are the
+    //    only destinations, so three reciprocals serve every normalisation
+    const Real rinv_m = j > 0 ? rcp_(r - (Real)1) : (Real)0;
+    const Real rinv_0 = m.inv_r;
+    const Real rinv_p = rcp_(r + (Real)1);
+#define AXILBM_PUSH(I)                                                                             \
+    {                                                                                              \
+        const Dest d = destination<I>(k, j, C.nr, C.nz, C.zper);                                   \
+        const int64_t dn = C.off + (int64_t)d.k * C.pitch + d.j;                                   \
+        const Real wr = (Real)w_of(I) * ((Real)d.j + (Real)0.5);                                   \
+        const Real iw = (Real)(1.0 / w_of(I)) * (d.j == j ? rinv_0 : (d.j > j ? rinv_p : rinv_m));   \
+        if (I != 0) {                                                                              \
+            const auto e = Codec::enc_f(fp[I], wr, iw);                                            \
+            S.fq_out[(int64_t)(d.dir - 1) * S.total + dn] = e;                                     \
+            if constexpr (Codec::kLedger) ff_add(ledger, -(float)Codec::dec_f(e, wr));             \
+        }                                                                                          \
+        S.g_out[(int64_t)d.dir * S.total + dn] = Codec::enc_g(gp[I], wr, iw);                     \
+    }
+    AXILBM_PUSH(0)
+    AXILBM_PUSH(1)
+    AXILBM_PUSH(2)
+    AXILBM_PUSH(3)
+    AXILBM_PUSH(4)
+    AXILBM_PUSH(5)
+    AXILBM_PUSH(6)
+    AXILBM_PUSH(7)
+    AXILBM_PUSH(8)
+#undef AXILBM_PUSH
+    // f_0: the collision's value (FP64), or the mass ledger: incoming total
+    // minus the outgoing f_1..8 as they will be read back
+    if constexpr (Codec::kLedger) {
+        const FF l = ff_norm(ledger);
+        S.f0_out[node] = make_float2(l.hi, l.lo);
+    } else {
+        S.f0_out[node] = fp[0];
+    }
+}
+
+// phi, rho, u_z, u_r, p of one case into dense FP64 arrays out[5][nz][nr].
+template <class Codec>
+__global__ void __launch_bounds__(kTR * 8)
+fields_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles, StateDev<Codec> S,
+              double* __restrict__ out) {
+    using Real = typename Codec::Real;
+    constexpr int TZ = 8;
+    constexpr int LD = kTR + 4;
+    __shared__ Real sphi[(TZ + 4) * LD];
+    const TileDev t = tiles[blockIdx.x];
+    const CaseDev& C = cases[t.c];
+    for (int idx = threadIdx.y * kTR + threadIdx.x; idx < (TZ + 4) * LD; idx += kTR * 8)
+        sphi[idx] = window_phi<Codec>(C, S, t, idx / LD, idx % LD);
+    __syncthreads();
+    const int j = t.j0 + threadIdx.x, k = t.k0 + threadIdx.y;
+    if (j >= C.nr || k >= C.nz) return;
+    const int64_t node = C.off + (int64_t)k * C.pitch + j;
+    const Real r = (Real)j + (Real)0.5;
+    Real g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = Codec::dec_g(S.g_in[(int64_t)i * S.total + node], (Real)w_of(i) * r);
+    Macro<Real> m;
+    node_macros<Real, LD>(C, sphi, threadIdx.y + 2, threadIdx.x + 2, j, g,
+                          C.p_coupling == 1 ? S.p_prev[node] : (Real)0, m);
+    const int64_t n = (int64_t)C.nz * C.nr, o = (int64_t)k * C.nr + j;
+    out[o] = (double)m.phi;
+    out[n + o] = (double)m.rho;
+    out[2 * n + o] = (double)m.uz;
+    out[3 * n + o] = (double)m.ur;
+    out[4 * n + o] = (double)m.p;
+}
+
+// Initial condition from phi0 (dense [nz][nr] FP64): f = f^eq(phi0, u = 0) of
+// Eq. 11, g = 0, chi^{-1} = (0, M phi0), p^{-1} = 0.  Writes the "in" buffers.
+template <class Codec>
+__global__ void init_kernel(CaseDev C, const double* __restrict__ phi0, StateDev<Codec> S,
+                            typename Codec::F0T* f0, typename Codec::PT* fq, typename Codec::PT* g) {
+    using Real = typename Codec::Real;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (j >= C.nr || k >= C.nz) return;
+    const int64_t node = C.off + (int64_t)k * C.pitch + j;
+    const Real phi = (Real)phi0[(int64_t)k * C.nr + j];
+    const Real r = (Real)j + (Real)0.5;
+    const CaseReal<Real>& P = case_params<Real>(C);
+    Real fe[9];
+    FF ledger{0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        fe[i] = (Real)w_of(i) * (r * phi + (Real)cr_of(i) * P.mob * phi * (Real)3);
+        if constexpr (Codec::kLedger) ff_add(ledger, (float)fe[i]);
+    }
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const Real wr = (Real)w_of(i) * r;
+        const auto e = Codec::enc_f(fe[i], wr, (Real)1 / wr);
+        fq[(int64_t)(i - 1) * S.total + node] = e;
+        if constexpr (Codec::kLedger) ff_add(ledger, -(float)Codec::dec_f(e, wr));
+    }
+    if constexpr (Codec::kLedger) {
+        const FF l = ff_norm(ledger);
+        f0[node] = make_float2(l.hi, l.lo);
+    } else {
+        f0[node] = fe[0];
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[(int64_t)i * S.total + node] = Codec::enc_g((Real)0, (Real)w_of(i) * r, (Real)1);
+    S.chi_z[node] = (Real)0;
+    S.chi_r[node] = P.mob * phi;
+    S.p_prev[node] = (Real)0;
+}
+
+// Decode the state of one case into FP64 arrays (f[9], g[9], aux[3], each [nz][nr]).
+template <class Codec>
+__global__ void get_state_kernel(CaseDev C, StateDev<Codec> S, double* f, double* g, double* aux) {
+    using Real = typename Codec::Real;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (j >= C.nr || k >= C.nz) return;
+    const int64_t node = C.off + (int64_t)k * C.pitch + j;
+    const int64_t n = (int64_t)C.nz * C.nr, o = (int64_t)k * C.nr + j;
+    const Real r = (Real)j + (Real)0.5;
+    if (f) {
+        if constexpr (Codec::kLedger) {
+            const float2 v = ((const float2*)S.f0_in)[node];
+            f[o] = (double)v.x + (double)v.y;
+        } else {
+            f[o] = (double)f0_value(S.f0_in[node]);
+        }
+        for (int i = 1; i < 9; ++i)
+            f[i * n + o] = (double)Codec::dec_f(S.fq_in[(int64_t)(i - 1) * S.total + node], (Real)w_of(i) * r);
+    }
+    if (g) {
+        for (int i = 0; i < 9; ++i)
+            g[i * n + o] = (double)Codec::dec_g(S.g_in[(int64_t)i * S.total + node], (Real)w_of(i) * r);
+    }
+    if (aux) {
+        aux[o] = (double)S.chi_z[node];
+        aux[n + o] = (double)S.chi_r[node];
+        aux[2 * n + o] = (double)S.p_prev[node];
+    }
+}
+
+// Encode FP64 arrays into the current ("in") state buffers of one case.
+template <class Codec>
+__global__ void set_state_kernel(CaseDev C, StateDev<Codec> S, typename Codec::F0T* f0, typename Codec::PT* fq,
+                                 typename Codec::PT* gq, const double* f, const double* g, const double* aux) {
+    using Real = typename Codec::Real;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (j >= C.nr || k >= C.nz) return;
+    const int64_t node = C.off + (int64_t)k * C.pitch + j;
+    const int64_t n = (int64_t)C.nz * C.nr, o = (int64_t)k * C.nr + j;
+    const Real r = (Real)j + (Real)0.5;
+    if (f) {
+        if constexpr (Codec::kLedger) {
+            // ledger = f_0 exactly as given (split into a float pair) plus the
+            // rounding of f_1..8, so the stored populations sum to the input sum
+            const double v0 = f[o];
+            FF ledger{(float)v0, (float)(v0 - (double)(float)v0)};
+            for (int i = 1; i < 9; ++i) {
+                const Real wr = (Real)w_of(i) * r;
+                const auto e = Codec::enc_f((Real)f[i * n + o], wr, (Real)1 / wr);
+                fq[(int64_t)(i - 1) * S.total + node] = e;
+                ff_add(ledger, (float)f[i * n + o]);
+                ff_add(ledger, (float)(f[i * n + o] - (double)(float)f[i * n + o]));
+                ff_add(ledger, -(float)Codec::dec_f(e, wr));
+            }
+            const FF l = ff_norm(ledger);
+            ((float2*)f0)[node] = make_float2(l.hi, l.lo);
+        } else {
+            for (int i = 1; i < 9; ++i) {
+                const Real wr = (Real)w_of(i) * r;
+                fq[(int64_t)(i - 1) * S.total + node] = Codec::enc_f((Real)f[i * n + o], wr, (Real)1 / wr);
+            }
+            ((double*)f0)[node] = f[o];
+        }
+    }
+    if (g) {
+        for (int i = 0; i < 9; ++i) {
+            const Real wr = (Real)w_of(i) * r;
+            gq[(int64_t)i * S.total + node] = Codec::enc_g((Real)g[i * n + o], wr, (Real)1 / wr);
+        }
+    }
+    if (aux) {
+        S.chi_z[node] = (Real)aux[o];
+        S.chi_r[node] = (Real)aux[n + o];
+        S.p_prev[node] = (Real)aux[2 * n + o];
+    }
+}
+
+// ---------------------------------------------------------------- host launchers
+template <class Codec>
+StateDev<Codec> make_state(const DeviceState& D, int parity) {
+    using PT = typename Codec::PT;
+    using F0T = typename Codec::F0T;
+    using Real = typename Codec::Real;
+    StateDev<Codec> S;
+    const int a = parity & 1, b = a ^ 1;
+    S.f0_in = (const F0T*)D.f0[a];
+    S.fq_in = (const PT*)D.fq[a];
+    S.g_in = (const PT*)D.g[a];
+    S.f0_out = (F0T*)D.f0[b];
+    S.fq_out = (PT*)D.fq[b];
+    S.g_out = (PT*)D.g[b];
+    S.chi_z = (Real*)D.chi_z;
+    S.chi_r = (Real*)D.chi_r;
+    S.p_prev = (Real*)D.p_prev;
+    S.total = D.total;
+    return S;
+}
+
+template <class Codec>
+cudaError_t launch_step_t(const DeviceState& D, int parity, int variant, const TileDev* tiles, int ntiles,
+                          cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    StateDev<Codec> S = make_state<Codec>(D, parity);
+    const CaseDev* cs = (const CaseDev*)D.cases;
+    switch (variant) {
+        case 0: step_kernel<Codec, 8><<<ntiles, dim3(kTR, 8), 0, st>>>(cs, tiles, S); break;
+        case 1: step_kernel<Codec, 16><<<ntiles, dim3(kTR, 16), 0, st>>>(cs, tiles, S); break;
+        default: step_kernel<Codec, 4><<<ntiles, dim3(kTR, 4), 0, st>>>(cs, tiles, S); break;
+    }
+    return cudaGetLastError();
+}
+
+template <class Codec>
+cudaError_t launch_fields_t(const DeviceState& D, int parity, const TileDev* tiles, int ntiles, double* out,
+                            cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    StateDev<Codec> S = make_state<Codec>(D, parity);
+    fields_kernel<Codec><<<ntiles, dim3(kTR, 8), 0, st>>>((const CaseDev*)D.cases, tiles, S, out);
+    return cudaGetLastError();
+}
+
+template <class Codec>
+cudaError_t launch_init_t(const DeviceState& D, int parity, const CaseDev& C, const double* phi0, cudaStream_t st) {
+    StateDev<Codec> S = make_state<Codec>(D, parity);
+    const int a = parity & 1;
+    dim3 grid((C.nr + 127) / 128, C.nz);
+    init_kernel<Codec><<<grid, 128, 0, st>>>(C, phi0, S, (typename Codec::F0T*)D.f0[a], (typename Codec::PT*)D.fq[a],
+                                             (typename Codec::PT*)D.g[a]);
+    return cudaGetLastError();
+}
+
+template <class Codec>
+cudaError_t launch_get_state_t(const DeviceState& D, int parity, const CaseDev& C, double* f, double* g, double* aux,
+                               cudaStream_t st) {
+    StateDev<Codec> S = make_state<Codec>(D, parity);
+    dim3 grid((C.nr + 127) / 128, C.nz);
+    get_state_kernel<Codec><<<grid, 128, 0, st>>>(C, S, f, g, aux);
+    return cudaGetLastError();
+}
+
+template <class Codec>
+cudaError_t launch_set_state_t(const DeviceState& D, int parity, const CaseDev& C, const double* f, const double* g,
+                               const double* aux, cudaStream_t st) {
+    StateDev<Codec> S = make_state<Codec>(D, parity);
+    const int a = parity & 1;
+    dim3 grid((C.nr + 127) / 128, C.nz);
+    set_state_kernel<Codec><<<grid, 128, 0, st>>>(C, S, (typename Codec::F0T*)D.f0[a], (typename Codec::PT*)D.fq[a],
+                                                  (typename Codec::PT*)D.g[a], f, g, aux);
+    return cudaGetLastError();
+}
+
+}  // namespace axilbm
+
+#define AXILBM_INSTANTIATE(NAME, CODEC)                                                                          \
+    namespace axilbm {                                                                                           \
+    cudaError_t launch_step_##NAME(const DeviceState& D, int parity, int variant, const TileDev* tiles,          \
+                                   int ntiles, cudaStream_t st) {                                                \
+        return launch_step_t<CODEC>(D, parity, variant, tiles, ntiles, st);                                      \
+    }                                                                                                            \
+    cudaError_t launch_fields_##NAME(const DeviceState& D, int parity, const TileDev* tiles, int ntiles,         \
+                                     double* out, cudaStream_t st) {                                             \
+        return launch_fields_t<CODEC>(D, parity, tiles, ntiles, out, st);                                        \
+    }                                                                                                            \
+    cudaError_t launch_init_##NAME(const DeviceState& D, int parity, const CaseDev& C, const double* phi0,       \
+                                   cudaStream_t st) {                                                            \
+        return launch_init_t<CODEC>(D, parity, C, phi0, st);                                                     \
+    }                                                                                                            \
+    cudaError_t launch_get_state_##NAME(const DeviceState& D, int parity, const CaseDev& C, double* f,           \
+                                        double* g, double* aux, cudaStream_t st) {                               \
+        return launch_get_state_t<CODEC>(D, parity, C, f, g, aux, st);                                           \
+    }                                                                                                            \
+    cudaError_t launch_set_state_##NAME(const DeviceState& D, int parity, const CaseDev& C, const double* f,     \
+                                        const double* g, const double* aux, cudaStream_t st) {                   \
+        return launch_set_state_t<CODEC>(D, parity, C, f, g, aux, st);                                           \
+    }                                                                                                            \
+    }

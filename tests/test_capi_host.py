@@ -1,0 +1,73 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point include/lbm.h declares, and the binding's marshalling
+matches the header's struct layouts."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1810_09299_gb300 import lbm, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(lbm.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    return lbm.lib()
+
+
+def test_library_exports_every_declared_symbol(L):
+    declared = _header_functions()
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(L, name), name
+    assert sorted(lbm.EXPORTS) == declared
+
+
+def test_struct_layouts_match_header():
+    # lbm_params: 6 int32 + 8 doubles + 18 doubles + 1 double
+    assert ctypes.sizeof(lbm.LbmParams) == 6 * 4 + 27 * 8
+    assert lbm.LbmParams.rho_l.offset == 24
+    assert ctypes.sizeof(lbm.LbmDiag) == 11 * 8
+
+
+def test_strerror_and_static_queries(L):
+    assert lbm.strerror(0) == "ok"
+    assert "invalid" in lbm.strerror(lbm.LBM_ERR_INVALID_ARG)
+    assert lbm.num_variants() >= 1
+    assert L.lbm_destroy(None) == 0
+    assert L.lbm_kernel_launches(None) == 0
+
+
+def test_invalid_arguments_rejected_before_device_work(L):
+    """Validation happens on the host before any CUDA call."""
+    h = ctypes.c_void_p()
+    bad = []
+    for kw in ({"nr": 1}, {"nz": 0}, {"rho_g": 0.0}, {"nu_l": -1.0}, {"W": 0.0}, {"mobility": 0.0},
+               {"sigma": -0.1}, {"precision": 7}, {"p_coupling": 3}):
+        c = workloads.static_drop(nr=16, nz=16, R=4.0)
+        c.update(kw)
+        bad.append(c)
+    c = workloads.static_drop(nr=16, nz=16, R=4.0)
+    c["sg"] = [2.5] * 9
+    bad.append(c)
+    for c in bad:
+        p = lbm.make_params(c)
+        assert L.lbm_create(ctypes.byref(p), None, ctypes.byref(h)) == lbm.LBM_ERR_INVALID_ARG
+    assert L.lbm_create(None, None, ctypes.byref(h)) == lbm.LBM_ERR_INVALID_ARG
+    p = lbm.make_params(workloads.static_drop(nr=16, nz=16, R=4.0))
+    assert L.lbm_batch_create(ctypes.byref(p), 0, None, ctypes.byref(h)) == lbm.LBM_ERR_INVALID_ARG
+    # mixed precisions in one batch
+    arr = (lbm.LbmParams * 2)(lbm.make_params(dict(workloads.static_drop(nr=16, nz=16, R=4.0), precision="fp32")),
+                              lbm.make_params(workloads.static_drop(nr=16, nz=16, R=4.0)))
+    assert L.lbm_batch_create(arr, 2, None, ctypes.byref(h)) == lbm.LBM_ERR_INVALID_ARG
