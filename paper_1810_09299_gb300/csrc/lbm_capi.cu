@@ -29,7 +29,8 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 int validate(const lbm_params& p) {
     if (p.nr < 2 || p.nz < 2) return LBM_ERR_INVALID_ARG;
-    if ((int64_t)p.nr * p.nz > (int64_t)1 << 34) return LBM_ERR_INVALID_ARG;
+    // 32-bit indexing inside a case: 9 planes of nz * pitch elements must fit
+    if ((int64_t)p.nz * ((p.nr + 31) / 32 * 32) * 9 >= ((int64_t)1 << 31)) return LBM_ERR_INVALID_ARG;
     if (p.z_periodic != 0 && p.z_periodic != 1) return LBM_ERR_INVALID_ARG;
     if (p.precision < LBM_FP64 || p.precision > LBM_MIX_BF16) return LBM_ERR_INVALID_ARG;
     if (p.p_coupling != LBM_P_EXACT && p.p_coupling != LBM_P_LAGGED) return LBM_ERR_INVALID_ARG;
@@ -195,6 +196,7 @@ CaseDev make_case(const lbm_params& p, int64_t off) {
     C.nr = p.nr;
     C.nz = p.nz;
     C.pitch = (p.nr + 31) / 32 * 32;
+    C.plane = p.nz * C.pitch;
     C.zper = p.z_periodic;
     C.p_coupling = p.p_coupling;
     C.off = off;

@@ -48,11 +48,18 @@ struct CaseReal {
     Real sg[9];   // hydrodynamic rates; entries flagged in sg_local are 1/tau_g(x)
 };
 
+// Memory layout (case-major): case c owns nodes [off, off + plane) of every
+// single-plane array (f_0, chi, p), the 8 planes [8 off, 8 (off + plane)) of
+// f_1..8 and the 9 planes [9 off, 9 (off + plane)) of g_0..8; inside a plane,
+// node (k, j) sits at k * pitch + j (pitch = nr rounded up to 32).  Indices
+// inside a case are 32-bit.
 struct CaseDev {
     int32_t nr, nz, pitch, zper;
     int32_t p_coupling;
     uint32_t sg_local;  // bit i set: sg[i] = 1/tau_g(x) from the local viscosity (Eq. 34)
-    int64_t off;        // element offset of the case inside every plane of the pooled arrays
+    int64_t off;        // node offset of the case (see above)
+    int32_t plane;      // nz * pitch
+    int32_t pad1;
     CaseReal<double> pd;
     CaseReal<float> pf;
 };
@@ -124,7 +131,8 @@ struct CodecH16 {
     using F0T = float2;
     static constexpr bool kLedger = true;
     static constexpr float kGScale = 256.0f;
-    __device__ static Real dec_f(PT v, Real wr) { return (__half2float(v) + 0.5f) * wr; }
+    // __fmul_rn: never fused into an FMA, so writer (ledger) and reader round alike
+    __device__ static Real dec_f(PT v, Real wr) { return __fmul_rn(__half2float(v) + 0.5f, wr); }
     __device__ static PT enc_f(Real v, Real, Real inv_wr) { return __float2half_rn(v * inv_wr - 0.5f); }
     __device__ static Real dec_g(PT v, Real wr) { return __half2float(v) * (wr * (1.0f / kGScale)); }
     __device__ static PT enc_g(Real v, Real, Real inv_wr) { return __float2half_rn(v * inv_wr * kGScale); }
@@ -135,7 +143,7 @@ struct CodecB16 {
     using PT = __nv_bfloat16;
     using F0T = float2;
     static constexpr bool kLedger = true;
-    __device__ static Real dec_f(PT v, Real wr) { return (__bfloat162float(v) + 0.5f) * wr; }
+    __device__ static Real dec_f(PT v, Real wr) { return __fmul_rn(__bfloat162float(v) + 0.5f, wr); }
     __device__ static PT enc_f(Real v, Real, Real inv_wr) { return __float2bfloat16_rn(v * inv_wr - 0.5f); }
     __device__ static Real dec_g(PT v, Real wr) { return __bfloat162float(v) * wr; }
     __device__ static PT enc_g(Real v, Real, Real inv_wr) { return __float2bfloat16_rn(v * inv_wr); }
@@ -151,16 +159,54 @@ struct StateDev {
     using F0T = typename Codec::F0T;
     using Real = typename Codec::Real;
     const F0T* f0_in;
-    const PT* fq_in;  // planes 0..7 hold f_1..f_8
-    const PT* g_in;   // planes 0..8 hold g_0..g_8
+    const PT* fq_in;   // f_1..f_8
+    const PT* g_in;    // g_0..g_8
     F0T* f0_out;
     PT* fq_out;
     PT* g_out;
-    Real* chi_z;  // chi^{n-1}, updated in place to chi^n
+    Real* chi_z;   // chi^{n-1}, updated in place to chi^n
     Real* chi_r;
     Real* p_prev;  // p^{n-1}, updated in place (lagged coupling only)
-    int64_t total;  // elements per plane of the pooled arrays
 };
+
+// The arrays of one case, with 32-bit indexing inside the case.
+template <class Codec>
+struct CaseView {
+    using PT = typename Codec::PT;
+    using F0T = typename Codec::F0T;
+    using Real = typename Codec::Real;
+    const F0T* f0_in;
+    const PT* fq_in;
+    const PT* g_in;
+    F0T* f0_out;
+    PT* fq_out;
+    PT* g_out;
+    Real* chi_z;
+    Real* chi_r;
+    Real* p_prev;
+    int plane, pitch;
+    __device__ __forceinline__ const PT& fin(int i, int loc) const { return fq_in[(i - 1) * plane + loc]; }
+    __device__ __forceinline__ const PT& gin(int i, int loc) const { return g_in[i * plane + loc]; }
+    __device__ __forceinline__ PT& fout(int i, int loc) const { return fq_out[(i - 1) * plane + loc]; }
+    __device__ __forceinline__ PT& gout(int i, int loc) const { return g_out[i * plane + loc]; }
+};
+
+template <class Codec>
+__device__ __forceinline__ CaseView<Codec> case_view(const StateDev<Codec>& S, const CaseDev& C) {
+    CaseView<Codec> v;
+    v.f0_in = S.f0_in + C.off;
+    v.fq_in = S.fq_in + 8 * C.off;
+    v.g_in = S.g_in + 9 * C.off;
+    v.f0_out = S.f0_out + C.off;
+    v.fq_out = S.fq_out + 8 * C.off;
+    v.g_out = S.g_out + 9 * C.off;
+    v.chi_z = S.chi_z + C.off;
+    v.chi_r = S.chi_r + C.off;
+    v.p_prev = S.p_prev + C.off;
+    v.plane = C.plane;
+    v.pitch = C.pitch;
+    return v;
+}
 
 // ---------------------------------------------------------------- ghost rules
 // Sec. 2.3: mirror about the axis (r = 0 lies between j = -1 and j = 0), mirror
@@ -185,15 +231,13 @@ __device__ __forceinline__ int ghost_z(int k, int nz, int zper) {
 
 // phi at an in-domain node from its stored populations (Eq. 16).
 template <class Codec>
-__device__ __forceinline__ typename Codec::Real node_phi(const StateDev<Codec>& S, int64_t node,
+__device__ __forceinline__ typename Codec::Real node_phi(const CaseView<Codec>& V, int loc,
                                                           typename Codec::Real r,
                                                           typename Codec::Real inv_r) {
     using Real = typename Codec::Real;
-    Real s = (Real)f0_value(S.f0_in[node]);
+    Real s = (Real)f0_value(V.f0_in[loc]);
 #pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        s += Codec::dec_f(S.fq_in[(int64_t)(i - 1) * S.total + node], (Real)w_of(i) * r);
-    }
+    for (int i = 1; i < 9; ++i) s += Codec::dec_f(V.fin(i, loc), (Real)w_of(i) * r);
     return s * inv_r;
 }
 

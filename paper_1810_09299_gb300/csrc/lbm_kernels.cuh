@@ -14,19 +14,34 @@ constexpr int kTR = 32;  // tile width along r = one warp
 
 // phi at window position (a, b) of tile t through the ghost rules.
 template <class Codec>
-__device__ __forceinline__ typename Codec::Real window_phi(const CaseDev& C, const StateDev<Codec>& S,
+__device__ __forceinline__ typename Codec::Real window_phi(const CaseDev& C, const CaseView<Codec>& V,
                                                             const TileDev& t, int a, int b) {
     using Real = typename Codec::Real;
     const int k = ghost_z(t.k0 - 2 + a, C.nz, C.zper);
     const int j = ghost_r(t.j0 - 2 + b, C.nr);
     const Real r = (Real)j + (Real)0.5;
-    return node_phi<Codec>(S, C.off + (int64_t)k * C.pitch + j, r, rcp_(r));
+    return node_phi<Codec>(V, k * C.pitch + j, r, rcp_(r));
 }
 
 // Minimum resident CTAs per SM requested from the register allocator.
 template <class Codec, int BZ>
 constexpr int step_min_blocks() {
     return sizeof(typename Codec::Real) == 8 ? 1 : (BZ >= 16 ? 1 : (BZ >= 8 ? 3 : 6));
+}
+
+// Store one post-collision population pair (f_I, g_I) at its destination
+// (local index `dl`, direction `dir`, destination radius normalisation
+// wr / iw) and account the stored f in the mass ledger.
+template <class Codec, int I>
+__device__ __forceinline__ void store_pair(const CaseView<Codec>& V, int dl, int dir, typename Codec::Real wr,
+                                           typename Codec::Real iw, typename Codec::Real fpi,
+                                           typename Codec::Real gpi, FF& ledger) {
+    if (I != 0) {
+        const auto e = Codec::enc_f(fpi, wr, iw);
+        V.fout(dir, dl) = e;
+        if constexpr (Codec::kLedger) ff_add(ledger, -(float)Codec::dec_f(e, wr));
+    }
+    V.gout(dir, dl) = Codec::enc_g(gpi, wr, iw);
 }
 
 // One time step for every node of every tile in `tiles`: one CTA per tile of
@@ -46,24 +61,25 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     __shared__ Real sphi[(TZ + 4) * LD];
     const TileDev t = tiles[blockIdx.x];
     const CaseDev& C = cases[t.c];
+    const CaseView<Codec> V = case_view<Codec>(S, C);
     const int j = t.j0 + threadIdx.x;
     const int k = t.k0 + threadIdx.y;
     const bool inside = (j < C.nr) && (k < C.nz);
-    const int64_t node = C.off + (int64_t)k * C.pitch + j;
+    const int loc = k * C.pitch + j;
 
     // 1. own-node loads, issued before anything waits on memory
     F0T f0raw{};
     PT fraw[8], graw[9];
     Real chz_prev = (Real)0, chr_prev = (Real)0, p_prev = (Real)0;
     if (inside) {
-        f0raw = S.f0_in[node];
+        f0raw = V.f0_in[loc];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) fraw[i] = S.fq_in[(int64_t)i * S.total + node];
+        for (int i = 1; i < 9; ++i) fraw[i - 1] = V.fin(i, loc);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) graw[i] = S.g_in[(int64_t)i * S.total + node];
-        chz_prev = S.chi_z[node];
-        chr_prev = S.chi_r[node];
-        if (C.p_coupling == 1) p_prev = S.p_prev[node];
+        for (int i = 0; i < 9; ++i) graw[i] = V.gin(i, loc);
+        chz_prev = V.chi_z[loc];
+        chr_prev = V.chi_r[loc];
+        if (C.p_coupling == 1) p_prev = V.p_prev[loc];
     }
     // 2. the ring of the phi window (two rows above and below, two columns
     //    left and right of the tile)
@@ -82,7 +98,7 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
             a = 2 + (q3 - c * TZ);
             b = c < 2 ? c : kTR + c;
         }
-        sphi[a * LD + b] = window_phi<Codec>(C, S, t, a, b);
+        sphi[a * LD + b] = window_phi<Codec>(C, V, t, a, b);
     }
     // 3. the node's own phi (Eq. 16); window cells outside the domain take the ghost rule
     const Real r = (Real)j + (Real)0.5;
@@ -97,7 +113,7 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
         }
         sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = sum * rcp_(r);
     } else {
-        sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = window_phi<Codec>(C, S, t, threadIdx.y + 2, threadIdx.x + 2);
+        sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = window_phi<Codec>(C, V, t, threadIdx.y + 2, threadIdx.x + 2);
     }
     __syncthreads();
     if (!inside) return;
@@ -116,47 +132,59 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     }
     Real fp[9], chz, chr;
     collide_f<Real>(C, m, f, chz_prev, chr_prev, chz, chr, fp);
-    S.chi_z[node] = chz;
-    S.chi_r[node] = chr;
-    if (C.p_coupling == 1) S.p_prev[node] = m.p;
+    V.chi_z[loc] = chz;
+    V.chi_r[loc] = chr;
+    if (C.p_coupling == 1) V.p_prev[loc] = m.p;
     Real gp[9];
     collide_g<Real>(C, m, gp);
 
-    // 5. streaming (Eq. 20) with the boundary rules; rows j-1, j, j+1 are the
-    //    only destinations, so three reciprocals serve every normalisation
-    const Real rinv_m = j > 0 ? rcp_(r - (Real)1) : (Real)0;
-    const Real rinv_0 = m.inv_r;
-    const Real rinv_p = rcp_(r + (Real)1);
-#define AXILBM_PUSH(I)                                                                             \
-    {                                                                                              \
-        const Dest d = destination<I>(k, j, C.nr, C.nz, C.zper);                                   \
-        const int64_t dn = C.off + (int64_t)d.k * C.pitch + d.j;                                   \
-        const Real wr = (Real)w_of(I) * ((Real)d.j + (Real)0.5);                                   \
-        const Real iw = (Real)(1.0 / w_of(I)) * (d.j == j ? rinv_0 : (d.j > j ? rinv_p : rinv_m));   \
-        if (I != 0) {                                                                              \
-            const auto e = Codec::enc_f(fp[I], wr, iw);                                            \
-            S.fq_out[(int64_t)(d.dir - 1) * S.total + dn] = e;                                     \
-            if constexpr (Codec::kLedger) ff_add(ledger, -(float)Codec::dec_f(e, wr));             \
-        }                                                                                          \
-        S.g_out[(int64_t)d.dir * S.total + dn] = Codec::enc_g(gp[I], wr, iw);                     \
+    // 5. streaming (Eq. 20).  Rows j-1, j, j+1 are the only destinations, so
+    //    three radii serve every normalisation.
+    const Real rinv[3] = {j > 0 ? rcp_(r - (Real)1) : (Real)0, m.inv_r, rcp_(r + (Real)1)};
+    const Real rdst[3] = {r - (Real)1, r, r + (Real)1};
+    const bool interior = (j >= 1) && (j + 1 < C.nr) && (k >= 1) && (k + 1 < C.nz);
+    if (interior) {
+        // every link lands on a neighbour inside the domain
+#define AXILBM_PUSH_FAST(I)                                                                              \
+    store_pair<Codec, I>(V, loc + cz_of(I) * C.pitch + cr_of(I), I, (Real)w_of(I) * rdst[cr_of(I) + 1],  \
+                         (Real)(1.0 / w_of(I)) * rinv[cr_of(I) + 1], fp[I], gp[I], ledger);
+        AXILBM_PUSH_FAST(0)
+        AXILBM_PUSH_FAST(1)
+        AXILBM_PUSH_FAST(2)
+        AXILBM_PUSH_FAST(3)
+        AXILBM_PUSH_FAST(4)
+        AXILBM_PUSH_FAST(5)
+        AXILBM_PUSH_FAST(6)
+        AXILBM_PUSH_FAST(7)
+        AXILBM_PUSH_FAST(8)
+#undef AXILBM_PUSH_FAST
+    } else {
+        // boundary nodes: wrap, bounce-back or axis reflection per link
+#define AXILBM_PUSH(I)                                                                                     \
+    {                                                                                                      \
+        const Dest d = destination<I>(k, j, C.nr, C.nz, C.zper);                                           \
+        const int s = d.j - j + 1;                                                                         \
+        store_pair<Codec, I>(V, d.k * C.pitch + d.j, d.dir, (Real)w_of(I) * rdst[s],                       \
+                             (Real)(1.0 / w_of(I)) * rinv[s], fp[I], gp[I], ledger);                       \
     }
-    AXILBM_PUSH(0)
-    AXILBM_PUSH(1)
-    AXILBM_PUSH(2)
-    AXILBM_PUSH(3)
-    AXILBM_PUSH(4)
-    AXILBM_PUSH(5)
-    AXILBM_PUSH(6)
-    AXILBM_PUSH(7)
-    AXILBM_PUSH(8)
+        AXILBM_PUSH(0)
+        AXILBM_PUSH(1)
+        AXILBM_PUSH(2)
+        AXILBM_PUSH(3)
+        AXILBM_PUSH(4)
+        AXILBM_PUSH(5)
+        AXILBM_PUSH(6)
+        AXILBM_PUSH(7)
+        AXILBM_PUSH(8)
 #undef AXILBM_PUSH
+    }
     // f_0: the collision's value (FP64), or the mass ledger: incoming total
     // minus the outgoing f_1..8 as they will be read back
     if constexpr (Codec::kLedger) {
         const FF l = ff_norm(ledger);
-        S.f0_out[node] = make_float2(l.hi, l.lo);
+        V.f0_out[loc] = make_float2(l.hi, l.lo);
     } else {
-        S.f0_out[node] = fp[0];
+        V.f0_out[loc] = fp[0];
     }
 }
 
@@ -171,19 +199,20 @@ fields_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ til
     __shared__ Real sphi[(TZ + 4) * LD];
     const TileDev t = tiles[blockIdx.x];
     const CaseDev& C = cases[t.c];
+    const CaseView<Codec> V = case_view<Codec>(S, C);
     for (int idx = threadIdx.y * kTR + threadIdx.x; idx < (TZ + 4) * LD; idx += kTR * 8)
-        sphi[idx] = window_phi<Codec>(C, S, t, idx / LD, idx % LD);
+        sphi[idx] = window_phi<Codec>(C, V, t, idx / LD, idx % LD);
     __syncthreads();
     const int j = t.j0 + threadIdx.x, k = t.k0 + threadIdx.y;
     if (j >= C.nr || k >= C.nz) return;
-    const int64_t node = C.off + (int64_t)k * C.pitch + j;
+    const int loc = k * C.pitch + j;
     const Real r = (Real)j + (Real)0.5;
     Real g[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = Codec::dec_g(S.g_in[(int64_t)i * S.total + node], (Real)w_of(i) * r);
+    for (int i = 0; i < 9; ++i) g[i] = Codec::dec_g(V.gin(i, loc), (Real)w_of(i) * r);
     Macro<Real> m;
-    node_macros<Real, LD>(C, sphi, threadIdx.y + 2, threadIdx.x + 2, j, g,
-                          C.p_coupling == 1 ? S.p_prev[node] : (Real)0, m);
+    node_macros<Real, LD>(C, sphi, threadIdx.y + 2, threadIdx.x + 2, j, g, C.p_coupling == 1 ? V.p_prev[loc] : (Real)0,
+                          m);
     const int64_t n = (int64_t)C.nz * C.nr, o = (int64_t)k * C.nr + j;
     out[o] = (double)m.phi;
     out[n + o] = (double)m.rho;
@@ -195,16 +224,19 @@ fields_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ til
 // Initial condition from phi0 (dense [nz][nr] FP64): f = f^eq(phi0, u = 0) of
 // Eq. 11, g = 0, chi^{-1} = (0, M phi0), p^{-1} = 0.  Writes the "in" buffers.
 template <class Codec>
-__global__ void init_kernel(CaseDev C, const double* __restrict__ phi0, StateDev<Codec> S,
-                            typename Codec::F0T* f0, typename Codec::PT* fq, typename Codec::PT* g) {
+__global__ void init_kernel(CaseDev C, const double* __restrict__ phi0, StateDev<Codec> S) {
     using Real = typename Codec::Real;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = blockIdx.y;
     if (j >= C.nr || k >= C.nz) return;
-    const int64_t node = C.off + (int64_t)k * C.pitch + j;
+    const CaseView<Codec> V = case_view<Codec>(S, C);
+    auto* f0 = const_cast<typename Codec::F0T*>(V.f0_in);
+    auto* fq = const_cast<typename Codec::PT*>(V.fq_in);
+    auto* gq = const_cast<typename Codec::PT*>(V.g_in);
+    const int loc = k * C.pitch + j;
+    const CaseReal<Real>& P = case_params<Real>(C);
     const Real phi = (Real)phi0[(int64_t)k * C.nr + j];
     const Real r = (Real)j + (Real)0.5;
-    const CaseReal<Real>& P = case_params<Real>(C);
     Real fe[9];
     FF ledger{0.0f, 0.0f};
 #pragma unroll
@@ -216,20 +248,20 @@ __global__ void init_kernel(CaseDev C, const double* __restrict__ phi0, StateDev
     for (int i = 1; i < 9; ++i) {
         const Real wr = (Real)w_of(i) * r;
         const auto e = Codec::enc_f(fe[i], wr, (Real)1 / wr);
-        fq[(int64_t)(i - 1) * S.total + node] = e;
+        fq[(i - 1) * C.plane + loc] = e;
         if constexpr (Codec::kLedger) ff_add(ledger, -(float)Codec::dec_f(e, wr));
     }
     if constexpr (Codec::kLedger) {
         const FF l = ff_norm(ledger);
-        f0[node] = make_float2(l.hi, l.lo);
+        f0[loc] = make_float2(l.hi, l.lo);
     } else {
-        f0[node] = fe[0];
+        f0[loc] = fe[0];
     }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) g[(int64_t)i * S.total + node] = Codec::enc_g((Real)0, (Real)w_of(i) * r, (Real)1);
-    S.chi_z[node] = (Real)0;
-    S.chi_r[node] = P.mob * phi;
-    S.p_prev[node] = (Real)0;
+    for (int i = 0; i < 9; ++i) gq[i * C.plane + loc] = Codec::enc_g((Real)0, (Real)w_of(i) * r, (Real)1);
+    V.chi_z[loc] = (Real)0;
+    V.chi_r[loc] = P.mob * phi;
+    V.p_prev[loc] = (Real)0;
 }
 
 // Decode the state of one case into FP64 arrays (f[9], g[9], aux[3], each [nz][nr]).
@@ -239,39 +271,41 @@ __global__ void get_state_kernel(CaseDev C, StateDev<Codec> S, double* f, double
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = blockIdx.y;
     if (j >= C.nr || k >= C.nz) return;
-    const int64_t node = C.off + (int64_t)k * C.pitch + j;
+    const CaseView<Codec> V = case_view<Codec>(S, C);
+    const int loc = k * C.pitch + j;
     const int64_t n = (int64_t)C.nz * C.nr, o = (int64_t)k * C.nr + j;
     const Real r = (Real)j + (Real)0.5;
     if (f) {
         if constexpr (Codec::kLedger) {
-            const float2 v = ((const float2*)S.f0_in)[node];
+            const float2 v = ((const float2*)V.f0_in)[loc];
             f[o] = (double)v.x + (double)v.y;
         } else {
-            f[o] = (double)f0_value(S.f0_in[node]);
+            f[o] = (double)f0_value(V.f0_in[loc]);
         }
-        for (int i = 1; i < 9; ++i)
-            f[i * n + o] = (double)Codec::dec_f(S.fq_in[(int64_t)(i - 1) * S.total + node], (Real)w_of(i) * r);
+        for (int i = 1; i < 9; ++i) f[i * n + o] = (double)Codec::dec_f(V.fin(i, loc), (Real)w_of(i) * r);
     }
     if (g) {
-        for (int i = 0; i < 9; ++i)
-            g[i * n + o] = (double)Codec::dec_g(S.g_in[(int64_t)i * S.total + node], (Real)w_of(i) * r);
+        for (int i = 0; i < 9; ++i) g[i * n + o] = (double)Codec::dec_g(V.gin(i, loc), (Real)w_of(i) * r);
     }
     if (aux) {
-        aux[o] = (double)S.chi_z[node];
-        aux[n + o] = (double)S.chi_r[node];
-        aux[2 * n + o] = (double)S.p_prev[node];
+        aux[o] = (double)V.chi_z[loc];
+        aux[n + o] = (double)V.chi_r[loc];
+        aux[2 * n + o] = (double)V.p_prev[loc];
     }
 }
 
 // Encode FP64 arrays into the current ("in") state buffers of one case.
 template <class Codec>
-__global__ void set_state_kernel(CaseDev C, StateDev<Codec> S, typename Codec::F0T* f0, typename Codec::PT* fq,
-                                 typename Codec::PT* gq, const double* f, const double* g, const double* aux) {
+__global__ void set_state_kernel(CaseDev C, StateDev<Codec> S, const double* f, const double* g, const double* aux) {
     using Real = typename Codec::Real;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = blockIdx.y;
     if (j >= C.nr || k >= C.nz) return;
-    const int64_t node = C.off + (int64_t)k * C.pitch + j;
+    const CaseView<Codec> V = case_view<Codec>(S, C);
+    auto* f0 = const_cast<typename Codec::F0T*>(V.f0_in);
+    auto* fq = const_cast<typename Codec::PT*>(V.fq_in);
+    auto* gq = const_cast<typename Codec::PT*>(V.g_in);
+    const int loc = k * C.pitch + j;
     const int64_t n = (int64_t)C.nz * C.nr, o = (int64_t)k * C.nr + j;
     const Real r = (Real)j + (Real)0.5;
     if (f) {
@@ -283,31 +317,31 @@ __global__ void set_state_kernel(CaseDev C, StateDev<Codec> S, typename Codec::F
             for (int i = 1; i < 9; ++i) {
                 const Real wr = (Real)w_of(i) * r;
                 const auto e = Codec::enc_f((Real)f[i * n + o], wr, (Real)1 / wr);
-                fq[(int64_t)(i - 1) * S.total + node] = e;
+                fq[(i - 1) * C.plane + loc] = e;
                 ff_add(ledger, (float)f[i * n + o]);
                 ff_add(ledger, (float)(f[i * n + o] - (double)(float)f[i * n + o]));
                 ff_add(ledger, -(float)Codec::dec_f(e, wr));
             }
             const FF l = ff_norm(ledger);
-            ((float2*)f0)[node] = make_float2(l.hi, l.lo);
+            ((float2*)f0)[loc] = make_float2(l.hi, l.lo);
         } else {
             for (int i = 1; i < 9; ++i) {
                 const Real wr = (Real)w_of(i) * r;
-                fq[(int64_t)(i - 1) * S.total + node] = Codec::enc_f((Real)f[i * n + o], wr, (Real)1 / wr);
+                fq[(i - 1) * C.plane + loc] = Codec::enc_f((Real)f[i * n + o], wr, (Real)1 / wr);
             }
-            ((double*)f0)[node] = f[o];
+            ((double*)f0)[loc] = f[o];
         }
     }
     if (g) {
         for (int i = 0; i < 9; ++i) {
             const Real wr = (Real)w_of(i) * r;
-            gq[(int64_t)i * S.total + node] = Codec::enc_g((Real)g[i * n + o], wr, (Real)1 / wr);
+            gq[i * C.plane + loc] = Codec::enc_g((Real)g[i * n + o], wr, (Real)1 / wr);
         }
     }
     if (aux) {
-        S.chi_z[node] = (Real)aux[o];
-        S.chi_r[node] = (Real)aux[n + o];
-        S.p_prev[node] = (Real)aux[2 * n + o];
+        V.chi_z[loc] = (Real)aux[o];
+        V.chi_r[loc] = (Real)aux[n + o];
+        V.p_prev[loc] = (Real)aux[2 * n + o];
     }
 }
 
@@ -328,7 +362,6 @@ StateDev<Codec> make_state(const DeviceState& D, int parity) {
     S.chi_z = (Real*)D.chi_z;
     S.chi_r = (Real*)D.chi_r;
     S.p_prev = (Real*)D.p_prev;
-    S.total = D.total;
     return S;
 }
 
@@ -358,10 +391,8 @@ cudaError_t launch_fields_t(const DeviceState& D, int parity, const TileDev* til
 template <class Codec>
 cudaError_t launch_init_t(const DeviceState& D, int parity, const CaseDev& C, const double* phi0, cudaStream_t st) {
     StateDev<Codec> S = make_state<Codec>(D, parity);
-    const int a = parity & 1;
     dim3 grid((C.nr + 127) / 128, C.nz);
-    init_kernel<Codec><<<grid, 128, 0, st>>>(C, phi0, S, (typename Codec::F0T*)D.f0[a], (typename Codec::PT*)D.fq[a],
-                                             (typename Codec::PT*)D.g[a]);
+    init_kernel<Codec><<<grid, 128, 0, st>>>(C, phi0, S);
     return cudaGetLastError();
 }
 
@@ -378,10 +409,8 @@ template <class Codec>
 cudaError_t launch_set_state_t(const DeviceState& D, int parity, const CaseDev& C, const double* f, const double* g,
                                const double* aux, cudaStream_t st) {
     StateDev<Codec> S = make_state<Codec>(D, parity);
-    const int a = parity & 1;
     dim3 grid((C.nr + 127) / 128, C.nz);
-    set_state_kernel<Codec><<<grid, 128, 0, st>>>(C, S, (typename Codec::F0T*)D.f0[a], (typename Codec::PT*)D.fq[a],
-                                                  (typename Codec::PT*)D.g[a], f, g, aux);
+    set_state_kernel<Codec><<<grid, 128, 0, st>>>(C, S, f, g, aux);
     return cudaGetLastError();
 }
 
