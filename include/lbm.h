@@ -48,12 +48,16 @@ typedef enum {
 
 /* Storage and arithmetic precision of a handle.
  *   LBM_FP64      populations and arithmetic in FP64.
- *   LBM_FP32      populations and arithmetic in FP32.
+ *   LBM_FP32      populations f_1..8 and g_0..8 in FP32, arithmetic in FP32.
  *   LBM_MIX_FP16  populations f_1..8 and g_0..8 stored as FP16 deviations
- *                 (f_i / (w_i r) - 1/2 and g_i / (w_i r), r of the storing node),
- *                 f_0 stored in FP32 so that each node's outgoing population sum is
- *                 kept exactly; arithmetic in FP32; reductions in FP64.
- *   LBM_MIX_BF16  as LBM_MIX_FP16 with bfloat16 storage. */
+ *                 (f_i / (w_i r) - 1/2 and 256 g_i / (w_i r), r of the storing
+ *                 node); arithmetic in FP32; reductions in FP64.
+ *   LBM_MIX_BF16  as LBM_MIX_FP16 with bfloat16 storage (no g scale).
+ * In the FP32 and 16-bit forms f_0 is stored as a pair of FP32 numbers holding
+ * the node's mass ledger: (sum of its incoming populations) minus (its stored
+ * outgoing f_1..8), accumulated with error-free FP32 additions, so the sum of
+ * all populations (the conserved sum of r phi, Eq. 16) changes only by round-off
+ * of about 2^-48. */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_MIX_FP16 = 2, LBM_MIX_BF16 = 3 } lbm_precision;
 
 /* Coupling of the pressure p and the radial velocity u_r (Eq. 32 uses p, Eq. 33
@@ -192,6 +196,27 @@ int32_t lbm_num_variants(void);
 
 /* Number of step-kernel launches this handle has issued (one per step). */
 int64_t lbm_kernel_launches(const lbm_handle* h);
+
+/* Allocation-free diagnostics reduction.  The paper has no counterpart: this
+ * is a service for callers that cannot allocate device memory at the moment
+ * they need the numbers (their device memory is held by their own pool, or
+ * they run a monitoring loop that must not pay for an allocation).
+ *   d_fields  device pointer, FP64 [5][nz][nr]: phi, rho, u_z, u_r, p (the
+ *             layout lbm_get_fields uses with mask 31), read only.
+ *   d_out     device pointer to 11 doubles, written with the lbm_diag record
+ *             (same definitions, same kernels and summation order as
+ *             lbm_diagnostics); step is copied into the first entry.
+ *   stream    cudaStream_t the work is enqueued on (NULL: default stream);
+ *             the call returns without synchronising.
+ * Nothing is allocated: the only scratch is a fixed 43,776-byte static device
+ * array of the library, held on every GPU that loads it until the process
+ * exits.  Requires nz, nr >= 1 and nz * nr <= 2^31 - 1, else
+ * LBM_ERR_INVALID_ARG.  The first call on a device looks up that array's
+ * device address on the current device; make that first call before any stream
+ * capture.  All calls share the array (its contents are fully rewritten by
+ * each call), so calls that overlap on the GPU, e.g. on two streams, race. */
+int lbm_diag_reduce_noalloc(const double* d_fields, int32_t nz, int32_t nr, int32_t z_periodic, double step,
+                            double* d_out, void* stream);
 
 /* Release every resource of the handle (NULL is ignored). */
 int lbm_destroy(lbm_handle* h);

@@ -3,13 +3,16 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <mutex>
+
+#include "../../include/lbm.h"
 #include "lbm_internal.h"
 
 namespace axilbm {
 
 namespace {
 
-constexpr int kDiagBlocks = 304;   // 2 x 152 SMs; fixed so the summation order is fixed
+constexpr int kDiagBlocks = kDiagPartials / 18;  // 2 x 152 SMs; fixed so the summation order is fixed
 constexpr int kDiagThreads = 256;
 
 // Neumaier compensated accumulation.
@@ -201,7 +204,7 @@ __global__ void shape_kernel(int shape, ShapeArgs A, int nz, int nr, double* __r
 
 }  // namespace
 
-int diag_partials_size() { return kDiagBlocks * 18; }
+int diag_partials_size() { return kDiagPartials; }
 
 cudaError_t launch_diag(const double* fields, int nz, int nr, int zper, double step, double* partials, double* out,
                         cudaStream_t st) {
@@ -219,3 +222,60 @@ cudaError_t launch_shape(int shape, const double* args, int nargs, int nz, int n
 }
 
 }  // namespace axilbm
+
+// ---------------------------------------------------------------- allocation-free reduction
+// lbm_diag_reduce_noalloc: the diagnostics reduction for callers that cannot
+// allocate device memory when they need the numbers (for example a caller
+// whose device memory is entirely held by its own pool, or a monitoring loop
+// that must not pay for an allocation).  Its only scratch, the per-block
+// partial sums, is a fixed static device array of this module.
+namespace {
+
+constexpr int kScratchDoubles = axilbm::kDiagPartials;  // 304 blocks x 18 doubles = 43,776 bytes
+constexpr int64_t kNoAllocMaxNodes = 2147483647;       // nz * nr must fit a signed 32-bit count
+constexpr int kMaxDevices = 64;
+
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) double g_diag_scratch[kScratchDoubles];
+
+std::mutex g_scratch_mutex;
+double* g_scratch_addr[kMaxDevices] = {};  // device address of g_diag_scratch, per device
+
+}  // namespace
+
+extern "C" int lbm_diag_reduce_noalloc(const double* d_fields, int32_t nz, int32_t nr, int32_t z_periodic,
+                                       double step, double* d_out, void* stream) {
+    if (!d_fields || !d_out || nz < 1 || nr < 1 || (z_periodic != 0 && z_periodic != 1))
+        return LBM_ERR_INVALID_ARG;
+    if ((int64_t)nz * nr > kNoAllocMaxNodes) return LBM_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) return LBM_ERR_INVALID_ARG;
+    double* scratch = nullptr;
+    {
+        // one-time set-up on this device (current device): the host-side name
+        // g_diag_scratch is not a device address, so look the address up
+        std::lock_guard<std::mutex> lock(g_scratch_mutex);
+        if (!g_scratch_addr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_diag_scratch);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                return LBM_ERR_CUDA;
+            }
+            g_scratch_addr[dev] = (double*)p;
+        }
+        scratch = g_scratch_addr[dev];
+    }
+    // Every partial slot is overwritten by the first kernel before the second
+    // reads it, so nothing from an earlier call needs clearing.
+    cudaError_t e = axilbm::launch_diag(d_fields, nz, nr, z_periodic, step, scratch, d_out, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}

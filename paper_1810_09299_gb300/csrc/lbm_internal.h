@@ -50,6 +50,7 @@ constexpr int kVariantTZ[kNumVariants] = {8, 16, 4};
 // Diagnostics (lbm_diag.cu): reduce dense FP64 fields of one case into a
 // 11-double record; `partials` is scratch of at least diag_partials_size()
 // doubles.  Deterministic (fixed block count and order).
+constexpr int kDiagPartials = 304 * 18;  // 304 blocks x 18 doubles
 int diag_partials_size();
 cudaError_t launch_diag(const double* fields, int nz, int nr, int zper, double step, double* partials,
                         double* out, cudaStream_t st);

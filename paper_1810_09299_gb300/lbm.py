@@ -35,7 +35,7 @@ EXPORTS = (
     "lbm_step", "lbm_get_fields", "lbm_case_get_fields", "lbm_diagnostics", "lbm_case_diagnostics",
     "lbm_get_state", "lbm_set_state", "lbm_checkpoint_size", "lbm_checkpoint_save",
     "lbm_checkpoint_load", "lbm_autotune", "lbm_set_variant", "lbm_num_variants",
-    "lbm_kernel_launches", "lbm_destroy", "lbm_strerror",
+    "lbm_kernel_launches", "lbm_destroy", "lbm_strerror", "lbm_diag_reduce_noalloc",
 )
 
 
@@ -100,6 +100,7 @@ def lib():
         "lbm_kernel_launches": (i64, [vp]),
         "lbm_destroy": (ctypes.c_int, [vp]),
         "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "lbm_diag_reduce_noalloc": (ctypes.c_int, [vp, i32, i32, i32, ctypes.c_double, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
