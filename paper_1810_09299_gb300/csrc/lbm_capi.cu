@@ -191,6 +191,21 @@ void fill_params(CaseReal<Real>& P, const lbm_params& p) {
     }
 }
 
+// The rate pattern of the paper's runs (Sec. 3.1): S^f = diag(1, 1, 1, s, s, s,
+// s, 1, 1) with one s; S^g = 1 except s1 = s7 = s8 derived from the local
+// viscosity.
+bool paper_rate_pattern(const lbm_params& p) {
+    for (int i : {0, 1, 2, 7, 8})
+        if (p.sf[i] != 1.0) return false;
+    for (int i = 4; i <= 6; ++i)
+        if (p.sf[i] != p.sf[3]) return false;
+    for (int i = 0; i < 9; ++i) {
+        const bool local = (i == 1 || i == 7 || i == 8);
+        if (local ? !(p.sg[i] < 0.0) : (p.sg[i] != 1.0)) return false;
+    }
+    return true;
+}
+
 CaseDev make_case(const lbm_params& p, int64_t off) {
     CaseDev C{};
     C.nr = p.nr;
@@ -267,6 +282,8 @@ int create_impl(const lbm_params* cases, int32_t n, void* stream, lbm_handle** o
         h->max_nodes = std::max<int64_t>(h->max_nodes, (int64_t)cases[c].nz * cases[c].nr);
     }
     h->D.total = off;
+    h->D.paper_rates = true;
+    for (int c = 0; c < n; ++c) h->D.paper_rates = h->D.paper_rates && paper_rate_pattern(cases[c]);
     h->case_steps.assign(n, 0);
     h->initialized.assign(n, 0);
     int rc = LBM_OK;

@@ -328,7 +328,12 @@ __device__ __forceinline__ void inverse_moments(const Real* m, Real* x) {
 
 // Everything before the collisions for node (k, j) of case C, from the
 // shared phi window (centred on (a, b)) and the node's decoded g.
-template <typename Real, int LD>
+//
+// PR ("paper rates"): the rate pattern of the paper's runs (Sec. 3.1) --
+// S^f = diag(1, 1, 1, s, s, s, s, 1, 1) and S^g = 1 except s1 = s7 = s8 =
+// 1/tau_g(x) -- is known at compile time, so unit-rate moments go straight to
+// their equilibrium and s_p = (s1 + s2 - s1 s2) / (2 s1 s2) = tau_g / 2.
+template <typename Real, int LD, bool PR = false>
 __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, int a, int b, int j, const Real* g,
                                             Real p_prev, Macro<Real>& m) {
     const CaseReal<Real>& P = case_params<Real>(C);
@@ -339,9 +344,14 @@ __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, 
     const Real rho_l = P.rho_l, rho_g = P.rho_g;
     m.rho = m.phi * rho_l + ((Real)1 - m.phi) * rho_g;                    // Eq. 17
     m.nu = m.phi * P.nu_l + ((Real)1 - m.phi) * P.nu_g;                  // Eq. 35
-    const Real sgv = rcp_((Real)3 * m.nu + (Real)0.5);                    // Eq. 34
+    const Real tau_g = (Real)3 * m.nu + (Real)0.5;                         // Eq. 34
+    const Real sgv = rcp_(tau_g);
+    if constexpr (PR) {
+        m.sg[1] = sgv;
+    } else {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) m.sg[i] = ((C.sg_local >> i) & 1u) ? sgv : P.sg[i];
+        for (int i = 0; i < 9; ++i) m.sg[i] = ((C.sg_local >> i) & 1u) ? sgv : P.sg[i];
+    }
     // Eq. 4 and mu~ = mu - k d_r phi / r
     const Real kap = P.kappa;
     const Real mu = (Real)4 * P.beta * m.phi * (m.phi - (Real)1) * (m.phi - (Real)0.5) - kap * m.lap;
@@ -358,8 +368,13 @@ __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, 
     const Real Jz = m.mg[3], Jr = m.mg[5], S0 = m.mg[0] - g[0];
     const Real drho = rho_l - rho_g;
     const Real dzrho = drho * m.gz, drrho = drho * m.gr;
-    const Real s1 = m.sg[1], s2 = m.sg[2];
-    const Real sp = div_(s1 + s2 - s1 * s2, (Real)2 * s1 * s2);
+    Real sp;
+    if constexpr (PR) {
+        sp = (Real)0.5 * tau_g;
+    } else {
+        const Real s1 = m.sg[1], s2 = m.sg[2];
+        sp = div_(s1 + s2 - s1 * s2, (Real)2 * s1 * s2);
+    }
     const Real r = m.r;
     m.uz = div_(Jz + (Real)0.5 * r * (Fsz + Gz), r * m.rho);              // Eq. 32 (z)
     const Real iDr = rcp_(r * m.rho + m.nu * m.rho * m.inv_r);
@@ -392,7 +407,7 @@ __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, 
 // ---------------------------------------------------------------- collisions
 // Phase field (Eq. 19 in moment space with Eq. 21-23).  chi = (r phi u_z,
 // r phi u_r + M phi); the time derivative of Eq. 38 uses chi^{n-1}.
-template <typename Real>
+template <typename Real, bool PR = false>
 __device__ __forceinline__ void collide_f(const CaseDev& C, const Macro<Real>& m, const Real* f, Real chi_z_prev,
                                           Real chi_r_prev, Real& chi_z, Real& chi_r, Real* fpost) {
     const CaseReal<Real>& P = case_params<Real>(C);
@@ -406,16 +421,28 @@ __device__ __forceinline__ void collide_f(const CaseDev& C, const Macro<Real>& m
     const Real meq[9] = {rphi, (Real)-2 * rphi, rphi, chi_z, -chi_z, chi_r, -chi_r, (Real)0, (Real)0};
     const Real mR[9] = {(Real)0, (Real)0, (Real)0, mR1, -mR1, mR2, -mR2, (Real)0, (Real)0};
     Real mp[9];
+    if constexpr (PR) {
+        // unit rates: m0 is conserved, m1, m2, m7, m8 take their equilibria
+        const Real s = P.sf[3], h = (Real)1 - (Real)0.5 * s;
+        mp[0] = rphi;
+        mp[1] = meq[1];
+        mp[2] = meq[2];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const Real s = P.sf[k];
-        mp[k] = mf[k] - s * (mf[k] - meq[k]) + ((Real)1 - (Real)0.5 * s) * mR[k];
+        for (int k = 3; k < 7; ++k) mp[k] = mf[k] - s * (mf[k] - meq[k]) + h * mR[k];
+        mp[7] = (Real)0;
+        mp[8] = (Real)0;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const Real s = P.sf[k];
+            mp[k] = mf[k] - s * (mf[k] - meq[k]) + ((Real)1 - (Real)0.5 * s) * mR[k];
+        }
     }
     inverse_moments<Real>(mp, fpost);
 }
 
 // Hydrodynamics (Eq. 24 in moment space with Eq. 36-37).
-template <typename Real>
+template <typename Real, bool PR = false>
 __device__ __forceinline__ void collide_g(const CaseDev& C, const Macro<Real>& m, Real* gpost) {
     const CaseReal<Real>& P = case_params<Real>(C);
     const Real r = m.r, rho = m.rho, uz = m.uz, ur = m.ur, p = m.p;
@@ -438,10 +465,19 @@ __device__ __forceinline__ void collide_g(const CaseDev& C, const Macro<Real>& m
                         (Real)(2.0 / 3.0) * (uz * dz_rr - ur * dr_rr),
                         (Real)(1.0 / 3.0) * (uz * dr_rr + ur * dz_rr)};
     Real mp[9];
+    if constexpr (PR) {
+        const Real s = m.sg[1], h = (Real)1 - (Real)0.5 * s;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const Real s = m.sg[k];
-        mp[k] = m.mg[k] - s * (m.mg[k] - meq[k]) + ((Real)1 - (Real)0.5 * s) * MT[k];
+        for (int k = 0; k < 9; ++k) {
+            if (k == 1 || k == 7 || k == 8) mp[k] = m.mg[k] - s * (m.mg[k] - meq[k]) + h * MT[k];
+            else mp[k] = meq[k] + (Real)0.5 * MT[k];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const Real s = m.sg[k];
+            mp[k] = m.mg[k] - s * (m.mg[k] - meq[k]) + ((Real)1 - (Real)0.5 * s) * MT[k];
+        }
     }
     inverse_moments<Real>(mp, gpost);
 }

@@ -23,6 +23,7 @@ struct DeviceState {
     void* p_prev;
     void* cases;  // CaseDev[ncases] on the device
     int64_t total;
+    bool paper_rates;  // every case uses the rate pattern of the paper's runs (Sec. 3.1)
 };
 
 #define AXILBM_DECLARE(NAME)                                                                                       \

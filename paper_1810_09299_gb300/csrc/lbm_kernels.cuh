@@ -23,10 +23,14 @@ __device__ __forceinline__ typename Codec::Real window_phi(const CaseDev& C, con
     return node_phi<Codec>(V, k * C.pitch + j, r, rcp_(r));
 }
 
-// Minimum resident CTAs per SM requested from the register allocator.
-template <class Codec, int BZ>
+// Minimum resident CTAs per SM requested from the register allocator: 32 warps
+// per SM (64 registers) for the FP32-arithmetic kernels with the paper's rate
+// pattern, which fit without spilling; 24 warps for general rates.
+template <class Codec, int BZ, bool PR>
 constexpr int step_min_blocks() {
-    return sizeof(typename Codec::Real) == 8 ? 1 : (BZ >= 16 ? 1 : (BZ >= 8 ? 3 : 6));
+    return sizeof(typename Codec::Real) == 8 ? 1
+           : PR ? (BZ >= 16 ? 2 : (BZ >= 8 ? 4 : 8))
+                : (BZ >= 16 ? 1 : (BZ >= 8 ? 3 : 6));
 }
 
 // Store one post-collision population pair (f_I, g_I) at its destination
@@ -49,8 +53,8 @@ __device__ __forceinline__ void store_pair(const CaseView<Codec>& V, int dl, int
 // the loads of its own node; the node's phi goes to the shared window straight
 // from those registers and only the two-node ring around the tile is
 // recomputed from neighbours' populations.
-template <class Codec, int BZ>
-__global__ void __launch_bounds__(kTR * BZ, (step_min_blocks<Codec, BZ>()))
+template <class Codec, int BZ, bool PR>
+__global__ void __launch_bounds__(kTR * BZ, (step_min_blocks<Codec, BZ, PR>()))
 step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles, StateDev<Codec> S) {
     using Real = typename Codec::Real;
     using PT = typename Codec::PT;
@@ -123,7 +127,7 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
 #pragma unroll
     for (int i = 0; i < 9; ++i) g[i] = Codec::dec_g(graw[i], (Real)w_of(i) * r);
     Macro<Real> m;
-    node_macros<Real, LD>(C, sphi, threadIdx.y + 2, threadIdx.x + 2, j, g, p_prev, m);
+    node_macros<Real, LD, PR>(C, sphi, threadIdx.y + 2, threadIdx.x + 2, j, g, p_prev, m);
     FF ledger{0.0f, 0.0f};
     if constexpr (Codec::kLedger) {
         ledger = FF{((const float2&)f0raw).x, ((const float2&)f0raw).y};
@@ -131,12 +135,12 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
         for (int i = 1; i < 9; ++i) ff_add(ledger, (float)f[i]);  // incoming total, exact
     }
     Real fp[9], chz, chr;
-    collide_f<Real>(C, m, f, chz_prev, chr_prev, chz, chr, fp);
+    collide_f<Real, PR>(C, m, f, chz_prev, chr_prev, chz, chr, fp);
     V.chi_z[loc] = chz;
     V.chi_r[loc] = chr;
     if (C.p_coupling == 1) V.p_prev[loc] = m.p;
     Real gp[9];
-    collide_g<Real>(C, m, gp);
+    collide_g<Real, PR>(C, m, gp);
 
     // 5. streaming (Eq. 20).  Rows j-1, j, j+1 are the only destinations, so
     //    three radii serve every normalisation.
@@ -365,17 +369,24 @@ StateDev<Codec> make_state(const DeviceState& D, int parity) {
     return S;
 }
 
+template <class Codec, bool PR>
+void launch_step_rates(int variant, int ntiles, cudaStream_t st, const CaseDev* cs, const TileDev* tiles,
+                       const StateDev<Codec>& S) {
+    switch (variant) {
+        case 0: step_kernel<Codec, 8, PR><<<ntiles, dim3(kTR, 8), 0, st>>>(cs, tiles, S); break;
+        case 1: step_kernel<Codec, 16, PR><<<ntiles, dim3(kTR, 16), 0, st>>>(cs, tiles, S); break;
+        default: step_kernel<Codec, 4, PR><<<ntiles, dim3(kTR, 4), 0, st>>>(cs, tiles, S); break;
+    }
+}
+
 template <class Codec>
 cudaError_t launch_step_t(const DeviceState& D, int parity, int variant, const TileDev* tiles, int ntiles,
                           cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
     StateDev<Codec> S = make_state<Codec>(D, parity);
     const CaseDev* cs = (const CaseDev*)D.cases;
-    switch (variant) {
-        case 0: step_kernel<Codec, 8><<<ntiles, dim3(kTR, 8), 0, st>>>(cs, tiles, S); break;
-        case 1: step_kernel<Codec, 16><<<ntiles, dim3(kTR, 16), 0, st>>>(cs, tiles, S); break;
-        default: step_kernel<Codec, 4><<<ntiles, dim3(kTR, 4), 0, st>>>(cs, tiles, S); break;
-    }
+    if (D.paper_rates) launch_step_rates<Codec, true>(variant, ntiles, st, cs, tiles, S);
+    else launch_step_rates<Codec, false>(variant, ntiles, st, cs, tiles, S);
     return cudaGetLastError();
 }
 
