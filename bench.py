@@ -24,6 +24,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -41,6 +42,11 @@ BYTES_PER_NODE = {
     "mix_bf16": 2 * (8 + 8 * 2 + 9 * 2 + 2 * 4),  # 100
 }
 DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf16": "f32 (bf16 storage)"}
+# DRAM bytes per node update of the step kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum over the nodes of the captured
+# launch; profiles/step_kernel_mix_fp16_batched64cases.md).  Scaled to a full
+# launch by the node count.  Kept only for the kernel that was captured.
+TRAFFIC_B_PER_NODE = {"mix_fp16": 90.27}
 
 
 def dist_env():
@@ -67,7 +73,7 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"axilbm_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -220,7 +226,7 @@ def run_cuda(args):
     import torch
     import torch.distributed as dist
 
-    from paper_1810_09299_gb300 import lbm
+    from paper_1810_09299_gb300 import lbm, shard
     from paper_1810_09299_gb300 import workloads as W
 
     rank, world, local = dist_env()
@@ -259,14 +265,10 @@ def run_cuda(args):
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     launches = sim.kernel_launches - launches0
-    ms = float(np.sum(times))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    total_nodes = nodes * world
-    value = total_nodes * args.steps / (ms * 1e-3) / 1e6
+    # weak scaling: every rank advances its own case set; the job's throughput
+    # is all ranks' nodes over the slowest rank's device time
+    value, ms, total_nodes = shard.job_throughput(nodes, args.steps, float(np.sum(times)),
+                                                  dist if world > 1 else None, torch.device("cuda", local))
     d = sim.diagnostics(0)
     peak, peak_kind = measured_peaks()
     per_launch_ms = float(np.mean(times))
@@ -284,7 +286,9 @@ def run_cuda(args):
                          "inputs larger than L2 (no flush)",
                    "variant": variant, "parallelism": f"independent cases per GPU x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (TRAFFIC_B_PER_NODE[prec] * nodes if prec in TRAFFIC_B_PER_NODE else None),
+                     "traffic_unit": "bytes per launch (ncu capture of 64 cases scaled by node count)",
                      "note": f"peak {peak_kind}; algorithmic bytes {BYTES_PER_NODE[prec]} B/node x {nodes} nodes "
                              f"per launch / mean CUDA-event launch duration"},
         "gpu_launches": int(launches),
@@ -297,6 +301,9 @@ def run_cuda(args):
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(cases, args, torch)
     if rank == 0 and not args.no_extra:
+        sim.close()
+        if args.workload == "batched" and prec != "fp32":
+            line["batched_fp32"] = batched_other(torch, args, "fp32")
         line["single_case_fp32"] = single_case(torch, "oscillating", "fp32", args.steps)
         line["single_case_fp64"] = single_case(torch, "oscillating", "fp64", max(4, args.steps // 4))
     if rank == 0 and not args.no_cpu:
@@ -336,6 +343,27 @@ def e2e(cases, args, torch):
     h2d = sum(p.nbytes for p in phis) / args.steps
     return {"value": nodes * args.steps / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": 88}
+
+
+def batched_other(torch, args, prec):
+    """The same batched case set in another precision (same timing method)."""
+    from paper_1810_09299_gb300 import lbm
+    cases = build_cases("batched", prec, 0, args.cases)
+    nodes = sum(c["nr"] * c["nz"] for c in cases)
+    sim = lbm.Simulation(cases)
+    for i, c in enumerate(cases):
+        sim.init_phase(i, c["shape"], c["shape_args"])
+    variant = sim.autotune(reps=2)
+    for _ in range(args.warmup):
+        sim.step(1)
+    times = time_steps(sim, torch, args.steps)
+    ms = float(np.mean(times))
+    peak, kind = measured_peaks()
+    ach = BYTES_PER_NODE[prec] * nodes / (ms * 1e-3) / 1e9
+    sim.close()
+    return {"precision": prec, "value": nodes / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
+            "variant": variant, "achieved_gbs": ach, "frac": ach / peak,
+            "bytes_per_node": BYTES_PER_NODE[prec]}
 
 
 def single_case(torch, workload, prec, steps):

@@ -1,0 +1,168 @@
+"""Physics checks of the CUDA path at the workloads' full sizes (needs a GB300).
+
+Each test runs a configuration to its physical end point and compares with
+what the paper and the mathematics fix: Laplace's law (Sec. 3.1), the
+Miller-Scriven frequency of Eq. 43-45 (Sec. 3.2, the paper reports errors up
+to 8.9 %), the Rayleigh-Plateau criterion (Sec. 3.3: a thread breaks for
+k < 1, not for k > 1), mass conservation, and agreement of the reduced
+precisions with the FP64 path (which matches the FP64 oracle to 1e-11).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import analytic as A
+from paper_1810_09299_gb300 import lbm, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(case, steps, every=0, probe=None):
+    sim = lbm.Simulation(case)
+    sim.init_case(0)
+    hist = []
+    if every:
+        for _ in range(steps // every):
+            sim.step(every)
+            hist.append(probe(sim))
+    else:
+        sim.step(steps)
+    return sim, hist
+
+
+def _volume_radius(phi):
+    r = np.arange(phi.shape[1])[None, :] + 0.5
+    return (3 * 2 * math.pi * np.sum(r * phi) / (4 * math.pi)) ** (1 / 3)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mix_fp16"])
+def test_static_drop_laplace_and_mass(prec):
+    """64 x 128 static drop, ratio 1000, 2000 steps: Laplace within 1 %,
+    mass drift below 1e-6 (reduced precisions) / 1e-12 (FP64)."""
+    case = dict(W.static_drop(), precision=prec)
+    sim = lbm.Simulation(case)
+    sim.init_case(0)
+    m0 = sim.diagnostics()["mass"]
+    sim.step(case["steps"])
+    d = sim.diagnostics()
+    lap = A.laplace_jump(case["sigma"], _volume_radius(sim.fields(which=("phi",))["phi"]))
+    print(prec, "dp", d["dp"], "laplace", lap, "umax", d["umax"], "mass drift", (d["mass"] - m0) / m0)
+    assert abs(d["dp"] - lap) / lap < 0.01
+    assert abs(d["mass"] - m0) / m0 < (1e-12 if prec == "fp64" else 1e-6)
+
+
+def _fit_frequency(ts, L, w0):
+    from scipy.optimize import curve_fit
+
+    def model(t, a, b, g, w, th):
+        return a + b * np.exp(-g * t) * np.cos(w * t + th)
+
+    tail = L[-len(L) // 3:].mean()
+    popt, _ = curve_fit(model, ts, L, p0=[tail, L[0] - tail, 1e-4, w0, 0.0], maxfev=40000)
+    return abs(popt[3])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mix_fp16"])
+def test_oscillating_drop_frequency(prec):
+    """128 x 256 P2 drop (R0 = 32, eps = 0.05, ratio 100, sigma = 0.005), 20,000
+    steps: the n = 2 frequency of the axis half-length within 10 % of Eq. 43."""
+    pytest.importorskip("scipy")
+    case = dict(W.oscillating_drop(), precision=prec)
+    sim, hist = _run(case, case["steps"], every=50,
+                     probe=lambda s: (s.diagnostics()["step"], s.diagnostics()["axis_half_length"]))
+    ts = np.array([h[0] for h in hist])
+    L = np.array([h[1] for h in hist])
+    Re = _volume_radius(sim.fields(which=("phi",))["phi"])
+    w_th = A.miller_scriven_frequency(2, Re, case["rho_l"], case["rho_g"], case["nu_l"], case["nu_g"],
+                                      case["sigma"])
+    sel = ts > 500
+    w = _fit_frequency(ts[sel], L[sel], w_th)
+    print(prec, "omega", w, "theory", w_th, "rel err", abs(w - w_th) / w_th)
+    assert abs(w - w_th) / w_th < 0.10
+
+
+def _axis_neck(sim):
+    phi = sim.fields(which=("phi",))["phi"]
+    return float(phi[:, 0].min())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mix_fp16"])
+def test_thread_breaks_up_below_rayleigh_limit(prec):
+    """Periodic thread R0 = 20, k = 2 pi R0 / lambda = 0.7 < 1, ratio 1000: the
+    neck on the axis pinches off (phi < 1/2) within 30,000 steps."""
+    case = dict(W.thread_breakup(), precision=prec)
+    assert A.rayleigh_unstable(20.0, case["nz"])
+    sim = lbm.Simulation(case)
+    sim.init_case(0)
+    t_break = None
+    for n in range(60):
+        sim.step(500)
+        if _axis_neck(sim) < 0.5:
+            t_break = (n + 1) * 500
+            break
+    t_cap = math.sqrt(20.0 ** 3 * case["rho_l"] / case["sigma"])
+    print(prec, "breakup step", t_break, "capillary units", None if t_break is None else t_break / t_cap)
+    assert t_break is not None
+
+
+def test_thread_stable_above_rayleigh_limit():
+    """Same thread with k = 1.25 > 1 (lambda shorter than the circumference): no breakup."""
+    case = dict(W.thread_breakup(k_wave=1.25), precision="mix_fp16")
+    assert not A.rayleigh_unstable(20.0, case["nz"])
+    sim = lbm.Simulation(case)
+    sim.init_case(0)
+    sim.step(30000)
+    assert _axis_neck(sim) > 0.5
+    assert sim.diagnostics()["nonfinite"] == 0
+
+
+def _bubble_centroid(sim):
+    phi = sim.fields(which=("phi",))["phi"]
+    gas = np.clip(1.0 - phi, 0.0, 1.0)
+    r = np.arange(phi.shape[1])[None, :] + 0.5
+    z = np.arange(phi.shape[0])[:, None] + 0.5
+    return float(np.sum(r * z * gas) / np.sum(r * gas))
+
+
+def test_rising_bubble_reduced_precisions_follow_fp64():
+    """256 x 1024 bubble (R = 32, ratio 1000, Eo = 10, Mo = 1e-3, M = 0.05), 20,000 steps:
+    the bubble rises; the FP32 and mixed-FP16 bubble-centroid histories stay
+    within 2 % of the rise of the FP64 path (which matches the oracle to 1e-11),
+    and so do their late rise velocities."""
+    hist = {}
+    for prec in ("fp64", "fp32", "mix_fp16"):
+        case = dict(W.rising_bubble(), precision=prec)
+        sim = lbm.Simulation(case)
+        sim.init_case(0)
+        zs = [_bubble_centroid(sim)]
+        for _ in range(20):
+            sim.step(1000)
+            zs.append(_bubble_centroid(sim))
+        assert sim.diagnostics()["nonfinite"] == 0
+        hist[prec] = np.array(zs)
+    rise = hist["fp64"][-1] - hist["fp64"][0]
+    v64 = (hist["fp64"][-1] - hist["fp64"][-5]) / 4000.0
+    print("bubble centroid", {k: v[[0, 10, 20]] for k, v in hist.items()}, "rise velocity (fp64)", v64)
+    assert rise > 1.0
+    for prec in ("fp32", "mix_fp16"):
+        assert np.max(np.abs(hist[prec] - hist["fp64"])) < 0.02 * rise, prec
+        v = (hist[prec][-1] - hist[prec][-5]) / 4000.0
+        assert abs(v - v64) < 0.05 * abs(v64), (prec, v, v64)
+
+
+def test_paper_static_drop_spurious_velocity():
+    """The paper's own static drop (Sec. 3.1): 200 x 100, R = 50, z-periodic,
+    rho_l = 1000, rho_g = 1, sigma = 1e-3, W = 4, M = 0.01, nu = 0.1.  The paper
+    reports |u|max about 1e-6.  The pressure jump settles within ~20,000 steps
+    (the liquid is 1000 times denser than the gas) to Laplace's law within 3 %."""
+    case = W.base_case(nr=100, nz=200, z_periodic=1, rho_l=1000.0, rho_g=1.0, nu_l=0.1, nu_g=0.1,
+                       sigma=0.001, W=4.0, mobility=0.01, shape="sphere", shape_args=[100.0, 50.0, 4.0])
+    sim = lbm.Simulation(case)
+    sim.init_case(0)
+    sim.step(20000)
+    d = sim.diagnostics()
+    lap = A.laplace_jump(0.001, _volume_radius(sim.fields(which=("phi",))["phi"]))
+    print("umax", d["umax"], "dp", d["dp"], "laplace", lap)
+    assert d["umax"] < 5e-6
+    assert abs(d["dp"] - lap) / lap < 0.03
