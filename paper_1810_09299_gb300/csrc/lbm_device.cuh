@@ -242,12 +242,19 @@ __device__ __forceinline__ typename Codec::Real node_phi(const CaseView<Codec>& 
 }
 
 // ---------------------------------------------------------------- arithmetic helpers
-// FP32: hardware reciprocal / division (at most 2 ulp, far below the FP32
-// rounding the method accumulates anyway); FP64: IEEE division.
-__device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
+// FP32: the hardware approximate reciprocal, division and square root (a few
+// ulp, far below the FP32 rounding the method accumulates over a run);
+// FP64: IEEE division and square root, as in the oracle.
+__device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
 __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double div_(double a, double b) { return a / b; }
+__device__ __forceinline__ float sqrt_(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 
 // ---------------------------------------------------------------- macroscopic part
 template <typename Real>
@@ -359,7 +366,7 @@ __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, 
     const Real Fsz = mut * m.gz, Fsr = mut * m.gr;
     const Real Gz = (m.rho - rho_l) * P.grav_z;
     // interface normal and lambda (Eq. 2)
-    const Real ign = rcp_(sqrt(m.gz * m.gz + m.gr * m.gr) + P.n_eps);
+    const Real ign = rcp_(sqrt_(m.gz * m.gz + m.gr * m.gr) + P.n_eps);
     m.nzn = m.gz * ign;
     m.nrn = m.gr * ign;
     m.lam = (Real)4 * m.phi * ((Real)1 - m.phi) * P.inv_W;
@@ -395,7 +402,7 @@ __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, 
         const Real qb = (Real)1 - A1 * cb + (Real)2 * A2 * ca * cb;
         const Real qc = -(A0 + A1 * ca - A2 * ca * ca);
         const Real disc = qb * qb - (Real)4 * qa * qc;
-        m.p = (disc >= (Real)0) ? div_((Real)-2 * qc, qb + sqrt(disc)) : div_(-qc, qb);
+        m.p = (disc >= (Real)0) ? div_((Real)-2 * qc, qb + sqrt_(disc)) : div_(-qc, qb);
         m.pstar = m.p;
         m.ur = ca + cb * m.p;
     }
