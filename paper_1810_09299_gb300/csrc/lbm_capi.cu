@@ -3,7 +3,9 @@
 // diagnostics read-back, state transfer, checkpoints and the launch-shape
 // autotuner.  All numerical work is done by the kernels in lbm_kernels.cuh and
 // lbm_diag.cu; this file only validates, allocates, launches and copies.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -93,6 +95,7 @@ struct lbm_sim {
     int64_t launches = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_variant = -1;
+    bool tma_ok = false;  // tensor maps could be encoded for every case
 };
 
 namespace {
@@ -255,6 +258,60 @@ void release(lbm_sim* h) {
     h->cap_stream = nullptr;
 }
 
+// Tensor maps of the TMA-staged step (see step_kernel_tma): per case and per
+// tile height (8, 16 rows): f_1..8 (3-D, parity 0/1), f_0 (2-D, parity 0/1),
+// g_0..8 (3-D, parity 0/1), chi_z, chi_r (2-D).  Returns false when the driver
+// entry point is missing or a map is rejected; the TMA variants are then unused.
+bool encode_tensor_maps(lbm_sim* h, std::vector<CUtensorMap>& maps) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return false;
+        }
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const int p = h->precision;
+    const size_t es = pt_size(p), er = real_size(p);
+    auto dtype = [](size_t bytes) {
+        return bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                          : (bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64);
+    };
+    maps.assign((size_t)h->ncases * 2 * kMapsPerCase, CUtensorMap{});
+    for (int c = 0; c < h->ncases; ++c) {
+        const CaseDev& C = h->cases[c];
+        for (int set = 0; set < 2; ++set) {
+            const cuuint32_t tz = set == 0 ? 8 : 16;
+            CUtensorMap* M = &maps[((size_t)c * 2 + set) * kMapsPerCase];
+            auto enc = [&](CUtensorMap* m, void* base, size_t bytes, int rank, cuuint32_t box0, cuuint32_t box1,
+                           cuuint32_t box2, cuuint32_t planes) {
+                const cuuint64_t dims[3] = {(cuuint64_t)C.pitch, (cuuint64_t)C.nz, planes};
+                const cuuint64_t strides[2] = {(cuuint64_t)C.pitch * bytes, (cuuint64_t)C.plane * bytes};
+                const cuuint32_t box[3] = {box0, box1, box2};
+                const cuuint32_t estr[3] = {1, 1, 1};
+                return encode(m, dtype(bytes), rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            };
+            for (int b = 0; b < 2; ++b) {
+                char* fq = (char*)h->D.fq[b] + 8 * C.off * es;
+                char* f0 = (char*)h->D.f0[b] + C.off * 8;
+                char* g = (char*)h->D.g[b] + 9 * C.off * es;
+                if (!enc(M + b, fq, es, 3, kTmaCols, tz + 4, 8, 8)) return false;
+                if (!enc(M + 2 + b, f0, 8, 2, kTmaCols, tz + 4, 1, 1)) return false;
+                if (!enc(M + 4 + b, g, es, 3, 32, tz, 9, 9)) return false;
+            }
+            if (!enc(M + 6, (char*)h->D.chi_z + C.off * er, er, 2, 32, tz, 1, 1)) return false;
+            if (!enc(M + 7, (char*)h->D.chi_r + C.off * er, er, 2, 32, tz, 1, 1)) return false;
+        }
+    }
+    return true;
+}
+
 int create_impl(const lbm_params* cases, int32_t n, void* stream, lbm_handle** out) {
     if (!out) return LBM_ERR_INVALID_ARG;
     *out = nullptr;
@@ -307,6 +364,19 @@ int create_impl(const lbm_params* cases, int32_t n, void* stream, lbm_handle** o
     A((void**)&h->state, 21 * (size_t)h->max_nodes * sizeof(double));
     A((void**)&h->partials, diag_partials_size() * sizeof(double));
     A((void**)&h->diag_out, 16 * sizeof(double));
+    A((void**)&h->D.status, 128);
+    if (rc == LBM_OK) {
+        std::vector<CUtensorMap> maps;
+        h->tma_ok = encode_tensor_maps(h, maps);
+        if (h->tma_ok) {
+            void* dm = nullptr;
+            A(&dm, maps.size() * sizeof(CUtensorMap));
+            if (rc == LBM_OK && cudaMemcpyAsync(dm, maps.data(), maps.size() * sizeof(CUtensorMap),
+                                                cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+                rc = LBM_ERR_CUDA;
+            h->D.tmaps = dm;
+        }
+    }
     if (rc == LBM_OK) {
         cudaError_t e = cudaMemcpyAsync(h->D.cases, h->cases.data(), n * sizeof(CaseDev), cudaMemcpyHostToDevice,
                                         h->stream);
@@ -375,6 +445,19 @@ int step_direct(lbm_sim* h, int64_t n) {
         if (e != cudaSuccess) return cuda_ok(h, e);
         h->parity ^= 1;
         h->launches += 1;
+    }
+    return LBM_OK;
+}
+
+// Device status word: set by a bounded wait that gave up (TMA-staged step).
+int check_status(lbm_sim* h) {
+    int st = 0;
+    if (cudaMemcpyAsync(&st, h->D.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return fail(h, LBM_ERR_CUDA);
+    if (st != 0) {
+        h->sticky = LBM_ERR_TIMEOUT;
+        return LBM_ERR_TIMEOUT;
     }
     return LBM_OK;
 }
@@ -462,6 +545,8 @@ int lbm_case_get_fields(lbm_handle* h, int32_t icase, int32_t mask, double* host
     if (rc != LBM_OK) return rc;
     if (check_case(h, icase) != LBM_OK || !host_out || mask <= 0 || mask > 31) return LBM_ERR_INVALID_ARG;
     if (!h->initialized[icase]) return LBM_ERR_STATE;
+    rc = check_status(h);
+    if (rc != LBM_OK) return rc;
     rc = cuda_ok(h, launch_fields_any(h, icase));
     if (rc != LBM_OK) return rc;
     const int64_t n = (int64_t)h->prm[icase].nz * h->prm[icase].nr;
@@ -483,6 +568,8 @@ int lbm_case_diagnostics(lbm_handle* h, int32_t icase, lbm_diag* out) {
     if (rc != LBM_OK) return rc;
     if (check_case(h, icase) != LBM_OK || !out) return LBM_ERR_INVALID_ARG;
     if (!h->initialized[icase]) return LBM_ERR_STATE;
+    rc = check_status(h);
+    if (rc != LBM_OK) return rc;
     rc = cuda_ok(h, launch_fields_any(h, icase));
     if (rc != LBM_OK) return rc;
     const lbm_params& p = h->prm[icase];
@@ -601,6 +688,7 @@ int lbm_set_variant(lbm_handle* h, int32_t variant) {
     int rc = enter(h);
     if (rc != LBM_OK) return rc;
     if (variant < 0 || variant >= kNumVariants) return LBM_ERR_INVALID_ARG;
+    if (kVariantTMA[variant] && !h->tma_ok) return LBM_ERR_INVALID_ARG;
     h->variant = variant;
     return LBM_OK;
 }
@@ -630,6 +718,7 @@ int lbm_autotune(lbm_handle* h, int32_t reps, int32_t* chosen) {
     float best = 1e30f;
     int best_v = h->variant;
     for (int v = 0; v < kNumVariants && rc == LBM_OK; ++v) {
+        if (kVariantTMA[v] && !h->tma_ok) continue;
         h->variant = v;
         rc = step_direct(h, 2);  // warm-up
         cudaEventRecord(e0, h->stream);

@@ -24,6 +24,8 @@ struct DeviceState {
     void* cases;  // CaseDev[ncases] on the device
     int64_t total;
     bool paper_rates;  // every case uses the rate pattern of the paper's runs (Sec. 3.1)
+    const void* tmaps;  // CUtensorMap[ncases][2 tile heights][kMapsPerCase] in device memory
+    int* status;        // device status word: nonzero after a bounded wait gave up
 };
 
 #define AXILBM_DECLARE(NAME)                                                                                       \
@@ -44,9 +46,16 @@ AXILBM_DECLARE(h16)
 AXILBM_DECLARE(b16)
 #undef AXILBM_DECLARE
 
-constexpr int kNumVariants = 3;
-// tile height along z of each step-kernel variant (tile width is one warp along r)
-constexpr int kVariantTZ[kNumVariants] = {8, 16, 4};
+constexpr int kNumVariants = 5;
+// tile height along z of each step-kernel variant (tile width is one warp along r);
+// variants 3 and 4 stage the tile through shared memory with TMA tensor loads
+constexpr int kVariantTZ[kNumVariants] = {8, 16, 4, 8, 16};
+constexpr bool kVariantTMA[kNumVariants] = {false, false, false, true, true};
+// tensor maps per case and tile height: f_1..8 (parity 0, 1), f_0 (parity 0, 1),
+// g_0..8 (parity 0, 1), chi_z, chi_r
+constexpr int kMapsPerCase = 8;
+constexpr int kTmaHalo = 8;   // columns loaded left of the tile (keeps x 16-byte aligned)
+constexpr int kTmaCols = 48;  // columns per loaded row: 8 + 32 + 8
 
 // Diagnostics (lbm_diag.cu): reduce dense FP64 fields of one case into a
 // 11-double record; `partials` is scratch of at least diag_partials_size()

@@ -48,6 +48,89 @@ __device__ __forceinline__ void store_pair(const CaseView<Codec>& V, int dl, int
     V.gout(dir, dl) = Codec::enc_g(gpi, wr, iw);
 }
 
+// Steps a4-a10 for one node whose raw stored values have been fetched: decode,
+// macroscopic recovery, both collisions, and the push with the boundary rules.
+template <class Codec, bool PR, int LD>
+__device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Codec>& V, const typename Codec::Real* sphi,
+                                            int a, int b, int k, int j, int loc,
+                                            const typename Codec::F0T& f0raw, const typename Codec::PT* fraw,
+                                            const typename Codec::PT* graw, typename Codec::Real chz_prev,
+                                            typename Codec::Real chr_prev, typename Codec::Real p_prev) {
+    using Real = typename Codec::Real;
+    const Real r = (Real)j + (Real)0.5;
+    Real f[9];
+    f[0] = (Real)f0_value(f0raw);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) f[i] = Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
+    Real g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = Codec::dec_g(graw[i], (Real)w_of(i) * r);
+    Macro<Real> m;
+    node_macros<Real, LD, PR>(C, sphi, a, b, j, g, p_prev, m);
+    FF ledger{0.0f, 0.0f};
+    if constexpr (Codec::kLedger) {
+        ledger = FF{((const float2&)f0raw).x, ((const float2&)f0raw).y};
+#pragma unroll
+        for (int i = 1; i < 9; ++i) ff_add(ledger, (float)f[i]);  // incoming total, exact
+    }
+    Real fp[9], chz, chr;
+    collide_f<Real, PR>(C, m, f, chz_prev, chr_prev, chz, chr, fp);
+    V.chi_z[loc] = chz;
+    V.chi_r[loc] = chr;
+    if (C.p_coupling == 1) V.p_prev[loc] = m.p;
+    Real gp[9];
+    collide_g<Real, PR>(C, m, gp);
+
+    // 5. streaming (Eq. 20).  Rows j-1, j, j+1 are the only destinations, so
+    //    three radii serve every normalisation.
+    const Real rinv[3] = {j > 0 ? rcp_(r - (Real)1) : (Real)0, m.inv_r, rcp_(r + (Real)1)};
+    const Real rdst[3] = {r - (Real)1, r, r + (Real)1};
+    const bool interior = (j >= 1) && (j + 1 < C.nr) && (k >= 1) && (k + 1 < C.nz);
+    if (interior) {
+        // every link lands on a neighbour inside the domain
+#define AXILBM_PUSH_FAST(I)                                                                              \
+    store_pair<Codec, I>(V, loc + cz_of(I) * C.pitch + cr_of(I), I, (Real)w_of(I) * rdst[cr_of(I) + 1],  \
+                         (Real)(1.0 / w_of(I)) * rinv[cr_of(I) + 1], fp[I], gp[I], ledger);
+        AXILBM_PUSH_FAST(0)
+        AXILBM_PUSH_FAST(1)
+        AXILBM_PUSH_FAST(2)
+        AXILBM_PUSH_FAST(3)
+        AXILBM_PUSH_FAST(4)
+        AXILBM_PUSH_FAST(5)
+        AXILBM_PUSH_FAST(6)
+        AXILBM_PUSH_FAST(7)
+        AXILBM_PUSH_FAST(8)
+#undef AXILBM_PUSH_FAST
+    } else {
+        // boundary nodes: wrap, bounce-back or axis reflection per link
+#define AXILBM_PUSH(I)                                                                                     \
+    {                                                                                                      \
+        const Dest d = destination<I>(k, j, C.nr, C.nz, C.zper);                                           \
+        const int s = d.j - j + 1;                                                                         \
+        store_pair<Codec, I>(V, d.k * C.pitch + d.j, d.dir, (Real)w_of(I) * rdst[s],                       \
+                             (Real)(1.0 / w_of(I)) * rinv[s], fp[I], gp[I], ledger);                       \
+    }
+        AXILBM_PUSH(0)
+        AXILBM_PUSH(1)
+        AXILBM_PUSH(2)
+        AXILBM_PUSH(3)
+        AXILBM_PUSH(4)
+        AXILBM_PUSH(5)
+        AXILBM_PUSH(6)
+        AXILBM_PUSH(7)
+        AXILBM_PUSH(8)
+#undef AXILBM_PUSH
+    }
+    // f_0: the collision's value (FP64), or the mass ledger: incoming total
+    // minus the outgoing f_1..8 as they will be read back
+    if constexpr (Codec::kLedger) {
+        const FF l = ff_norm(ledger);
+        V.f0_out[loc] = make_float2(l.hi, l.lo);
+    } else {
+        V.f0_out[loc] = fp[0];
+    }
+}
+
 // One time step for every node of every tile in `tiles`: one CTA per tile of
 // BZ rows (z) x 32 columns (r), one node per thread.  Each thread first issues
 // the loads of its own node; the node's phi goes to the shared window straight
@@ -122,74 +205,116 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     __syncthreads();
     if (!inside) return;
 
-    // 4. macroscopic recovery and the two collisions
-    Real g[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = Codec::dec_g(graw[i], (Real)w_of(i) * r);
-    Macro<Real> m;
-    node_macros<Real, LD, PR>(C, sphi, threadIdx.y + 2, threadIdx.x + 2, j, g, p_prev, m);
-    FF ledger{0.0f, 0.0f};
-    if constexpr (Codec::kLedger) {
-        ledger = FF{((const float2&)f0raw).x, ((const float2&)f0raw).y};
-#pragma unroll
-        for (int i = 1; i < 9; ++i) ff_add(ledger, (float)f[i]);  // incoming total, exact
-    }
-    Real fp[9], chz, chr;
-    collide_f<Real, PR>(C, m, f, chz_prev, chr_prev, chz, chr, fp);
-    V.chi_z[loc] = chz;
-    V.chi_r[loc] = chr;
-    if (C.p_coupling == 1) V.p_prev[loc] = m.p;
-    Real gp[9];
-    collide_g<Real, PR>(C, m, gp);
+    node_update<Codec, PR, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw, graw, chz_prev,
+                               chr_prev, p_prev);
+}
 
-    // 5. streaming (Eq. 20).  Rows j-1, j, j+1 are the only destinations, so
-    //    three radii serve every normalisation.
-    const Real rinv[3] = {j > 0 ? rcp_(r - (Real)1) : (Real)0, m.inv_r, rcp_(r + (Real)1)};
-    const Real rdst[3] = {r - (Real)1, r, r + (Real)1};
-    const bool interior = (j >= 1) && (j + 1 < C.nr) && (k >= 1) && (k + 1 < C.nz);
-    if (interior) {
-        // every link lands on a neighbour inside the domain
-#define AXILBM_PUSH_FAST(I)                                                                              \
-    store_pair<Codec, I>(V, loc + cz_of(I) * C.pitch + cr_of(I), I, (Real)w_of(I) * rdst[cr_of(I) + 1],  \
-                         (Real)(1.0 / w_of(I)) * rinv[cr_of(I) + 1], fp[I], gp[I], ledger);
-        AXILBM_PUSH_FAST(0)
-        AXILBM_PUSH_FAST(1)
-        AXILBM_PUSH_FAST(2)
-        AXILBM_PUSH_FAST(3)
-        AXILBM_PUSH_FAST(4)
-        AXILBM_PUSH_FAST(5)
-        AXILBM_PUSH_FAST(6)
-        AXILBM_PUSH_FAST(7)
-        AXILBM_PUSH_FAST(8)
-#undef AXILBM_PUSH_FAST
-    } else {
-        // boundary nodes: wrap, bounce-back or axis reflection per link
-#define AXILBM_PUSH(I)                                                                                     \
-    {                                                                                                      \
-        const Dest d = destination<I>(k, j, C.nr, C.nz, C.zper);                                           \
-        const int s = d.j - j + 1;                                                                         \
-        store_pair<Codec, I>(V, d.k * C.pitch + d.j, d.dir, (Real)w_of(I) * rdst[s],                       \
-                             (Real)(1.0 / w_of(I)) * rinv[s], fp[I], gp[I], ledger);                       \
+// Shared-memory layout of the TMA-staged step for tile height TZ.
+template <class Codec, int TZ>
+struct TmaTile {
+    using PT = typename Codec::PT;
+    using F0T = typename Codec::F0T;
+    using Real = typename Codec::Real;
+    static constexpr int HR = TZ + 4;          // rows k0-2 .. k0+TZ+1
+    static constexpr int HX = kTmaCols;        // columns j0-8 .. j0+39
+    static constexpr int LD = kTR + 4;         // phi window row length
+    static constexpr size_t al(size_t b) { return (b + 127) / 128 * 128; }
+    static constexpr size_t fq_bytes = (size_t)8 * HR * HX * sizeof(PT);
+    static constexpr size_t f0_bytes = (size_t)HR * HX * sizeof(F0T);
+    static constexpr size_t g_bytes = (size_t)9 * TZ * kTR * sizeof(PT);
+    static constexpr size_t chi_bytes = (size_t)TZ * kTR * sizeof(Real);
+    static constexpr size_t off_fq = 0;
+    static constexpr size_t off_f0 = al(off_fq + fq_bytes);
+    static constexpr size_t off_g = al(off_f0 + f0_bytes);
+    static constexpr size_t off_chz = al(off_g + g_bytes);
+    static constexpr size_t off_chr = al(off_chz + chi_bytes);
+    static constexpr size_t off_phi = al(off_chr + chi_bytes);
+    static constexpr size_t off_bar = al(off_phi + (size_t)HR * LD * sizeof(Real));
+    static constexpr size_t bytes = off_bar + 128;
+    static constexpr uint32_t tx_bytes = (uint32_t)(fq_bytes + f0_bytes + g_bytes + 2 * chi_bytes);
+};
+
+// The same step as step_kernel, with the tile's inputs staged in shared memory
+// by TMA tensor loads: f_0..8 over the tile plus two rows above and below and
+// eight columns either side (x stays 16-byte aligned; cells outside the arrays
+// read as zero and are never used), g and chi over the tile.  One thread issues
+// the five copies; all threads wait on one mbarrier (bounded).  The phi window
+// (Eq. 16 + ghost rules) is then computed from shared memory; only ghost cells
+// that wrap around a periodic z boundary read global memory.
+template <class Codec, int BZ, bool PR>
+__global__ void __launch_bounds__(kTR * BZ, (step_min_blocks<Codec, BZ, PR>()))
+step_kernel_tma(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles, StateDev<Codec> S,
+                const CUtensorMap* __restrict__ maps, int map_set, int parity, int* __restrict__ status) {
+    using Real = typename Codec::Real;
+    using PT = typename Codec::PT;
+    using F0T = typename Codec::F0T;
+    using L = TmaTile<Codec, BZ>;
+    constexpr int TZ = BZ, HR = L::HR, HX = L::HX, LD = L::LD;
+    extern __shared__ __align__(128) unsigned char smem[];
+    PT* s_fq = (PT*)(smem + L::off_fq);      // [8][HR][HX]
+    F0T* s_f0 = (F0T*)(smem + L::off_f0);    // [HR][HX]
+    PT* s_g = (PT*)(smem + L::off_g);        // [9][TZ][32]
+    Real* s_chz = (Real*)(smem + L::off_chz);  // [TZ][32]
+    Real* s_chr = (Real*)(smem + L::off_chr);
+    Real* sphi = (Real*)(smem + L::off_phi);   // [HR][LD]
+    uint64_t* bar = (uint64_t*)(smem + L::off_bar);
+
+    const TileDev t = tiles[blockIdx.x];
+    const CaseDev& C = cases[t.c];
+    const CaseView<Codec> V = case_view<Codec>(S, C);
+    const int tid = threadIdx.y * kTR + threadIdx.x;
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+        const CUtensorMap* M = maps + ((size_t)t.c * 2 + map_set) * kMapsPerCase;
+        for (int q : {parity, 2 + parity, 4 + parity, 6, 7}) tensormap_acquire(M + q);
+        mbar_expect_tx(bar, L::tx_bytes);
+        tma_load_3d(s_fq, M + parity, t.j0 - kTmaHalo, t.k0 - 2, 0, bar);
+        tma_load_2d(s_f0, M + 2 + parity, t.j0 - kTmaHalo, t.k0 - 2, bar);
+        tma_load_3d(s_g, M + 4 + parity, t.j0, t.k0, 0, bar);
+        tma_load_2d(s_chz, M + 6, t.j0, t.k0, bar);
+        tma_load_2d(s_chr, M + 7, t.j0, t.k0, bar);
     }
-        AXILBM_PUSH(0)
-        AXILBM_PUSH(1)
-        AXILBM_PUSH(2)
-        AXILBM_PUSH(3)
-        AXILBM_PUSH(4)
-        AXILBM_PUSH(5)
-        AXILBM_PUSH(6)
-        AXILBM_PUSH(7)
-        AXILBM_PUSH(8)
-#undef AXILBM_PUSH
+    const bool ok = mbar_wait_bounded(bar, 0, status, 1 << 22);
+
+    // phi window from the staged populations
+    if (ok) {
+        for (int idx = tid; idx < HR * LD; idx += kTR * BZ) {
+            const int a = idx / LD, b = idx - (idx / LD) * LD;
+            const int km = ghost_z(t.k0 - 2 + a, C.nz, C.zper);
+            const int jm = ghost_r(t.j0 - 2 + b, C.nr);
+            const int sa = km - (t.k0 - 2), sx = jm - (t.j0 - kTmaHalo);
+            const Real r = (Real)jm + (Real)0.5;
+            Real phi;
+            if (sa >= 0 && sa < HR && sx >= 0 && sx < HX) {
+                const int o = sa * HX + sx;
+                Real sum = (Real)f0_value(s_f0[o]);
+#pragma unroll
+                for (int i = 1; i < 9; ++i) sum += Codec::dec_f(s_fq[(i - 1) * HR * HX + o], (Real)w_of(i) * r);
+                phi = sum * rcp_(r);
+            } else {
+                phi = node_phi<Codec>(V, km * C.pitch + jm, r, rcp_(r));
+            }
+            sphi[idx] = phi;
+        }
     }
-    // f_0: the collision's value (FP64), or the mass ledger: incoming total
-    // minus the outgoing f_1..8 as they will be read back
-    if constexpr (Codec::kLedger) {
-        const FF l = ff_norm(ledger);
-        V.f0_out[loc] = make_float2(l.hi, l.lo);
-    } else {
-        V.f0_out[loc] = fp[0];
-    }
+    __syncthreads();
+    const int j = t.j0 + threadIdx.x;
+    const int k = t.k0 + threadIdx.y;
+    if (!ok || j >= C.nr || k >= C.nz) return;
+    const int loc = k * C.pitch + j;
+    const int o = (threadIdx.y + 2) * HX + threadIdx.x + kTmaHalo;
+    const F0T f0raw = s_f0[o];
+    PT fraw[8], graw[9];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) fraw[i - 1] = s_fq[(i - 1) * HR * HX + o];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) graw[i] = s_g[(i * TZ + threadIdx.y) * kTR + threadIdx.x];
+    const Real chz_prev = s_chz[threadIdx.y * kTR + threadIdx.x];
+    const Real chr_prev = s_chr[threadIdx.y * kTR + threadIdx.x];
+    const Real p_prev = C.p_coupling == 1 ? V.p_prev[loc] : (Real)0;
+    node_update<Codec, PR, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw, graw, chz_prev,
+                               chr_prev, p_prev);
 }
 
 // phi, rho, u_z, u_r, p of one case into dense FP64 arrays out[5][nz][nr].
@@ -369,13 +494,28 @@ StateDev<Codec> make_state(const DeviceState& D, int parity) {
     return S;
 }
 
+template <class Codec, int BZ, bool PR>
+void launch_tma(int ntiles, cudaStream_t st, const CaseDev* cs, const TileDev* tiles, const StateDev<Codec>& S,
+                const DeviceState& D, int parity) {
+    using L = TmaTile<Codec, BZ>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(step_kernel_tma<Codec, BZ, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+        attr_set = true;
+    }
+    step_kernel_tma<Codec, BZ, PR><<<ntiles, dim3(kTR, BZ), L::bytes, st>>>(
+        cs, tiles, S, (const CUtensorMap*)D.tmaps, BZ == 8 ? 0 : 1, parity, D.status);
+}
+
 template <class Codec, bool PR>
 void launch_step_rates(int variant, int ntiles, cudaStream_t st, const CaseDev* cs, const TileDev* tiles,
-                       const StateDev<Codec>& S) {
+                       const StateDev<Codec>& S, const DeviceState& D, int parity) {
     switch (variant) {
         case 0: step_kernel<Codec, 8, PR><<<ntiles, dim3(kTR, 8), 0, st>>>(cs, tiles, S); break;
         case 1: step_kernel<Codec, 16, PR><<<ntiles, dim3(kTR, 16), 0, st>>>(cs, tiles, S); break;
-        default: step_kernel<Codec, 4, PR><<<ntiles, dim3(kTR, 4), 0, st>>>(cs, tiles, S); break;
+        case 2: step_kernel<Codec, 4, PR><<<ntiles, dim3(kTR, 4), 0, st>>>(cs, tiles, S); break;
+        case 3: launch_tma<Codec, 8, PR>(ntiles, st, cs, tiles, S, D, parity); break;
+        default: launch_tma<Codec, 16, PR>(ntiles, st, cs, tiles, S, D, parity); break;
     }
 }
 
@@ -385,8 +525,8 @@ cudaError_t launch_step_t(const DeviceState& D, int parity, int variant, const T
     if (ntiles <= 0) return cudaSuccess;
     StateDev<Codec> S = make_state<Codec>(D, parity);
     const CaseDev* cs = (const CaseDev*)D.cases;
-    if (D.paper_rates) launch_step_rates<Codec, true>(variant, ntiles, st, cs, tiles, S);
-    else launch_step_rates<Codec, false>(variant, ntiles, st, cs, tiles, S);
+    if (D.paper_rates) launch_step_rates<Codec, true>(variant, ntiles, st, cs, tiles, S, D, parity);
+    else launch_step_rates<Codec, false>(variant, ntiles, st, cs, tiles, S, D, parity);
     return cudaGetLastError();
 }
 

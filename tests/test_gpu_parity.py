@@ -148,6 +148,21 @@ def test_variants_graph_and_direct_are_bit_identical():
         assert np.array_equal(f[k], ref[k]), k
 
 
+@pytest.mark.parametrize("prec", ["fp32", "mix_fp16", "mix_bf16"])
+def test_launch_variants_bit_identical_reduced_precision(prec):
+    """Every launch shape (register-staged and TMA-staged tiles) computes the
+    same numbers, also for periodic z (ghost rows wrap around)."""
+    for case in (dict(W.static_drop(nr=45, nz=70, R=12.0), precision=prec),
+                 dict(W.thread_breakup(nr=40, R0=12.0), precision=prec)):
+        ref = None
+        for v in range(lbm.num_variants()):
+            f = run_gpu(case, 40, variant=v).fields()
+            if ref is None:
+                ref = f
+            for k in FIELDS:
+                assert np.array_equal(f[k], ref[k]), (prec, v, k)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "mix_fp16"])
 def test_batch_equals_single_cases(prec):
     cases = [dict(W.static_drop(nr=40, nz=64, R=10.0), precision=prec),
