@@ -6,7 +6,8 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
 Default workload: the batched case set (512 independent static and
 oscillating droplet cases, grids drawn from seed 20181022 between 64 x 128 and
 256 x 512, density ratios 10/100/1000) advancing together, one kernel launch
-per time step, 16-bit deviation-stored populations with FP32 arithmetic.
+per time step, FP32 populations and arithmetic (FP64 mass ledger and
+reductions).  The same line reports the 16-bit deviation-stored form.
 Per-step inputs (~2.5-4.5 GB of populations) are far larger than L2 (129 MB),
 so no flush is needed between steps.  The same JSON line also reports the
 plain FP32 single-case path on the 128 x 256 oscillating drop (L2 flushed
@@ -44,9 +45,9 @@ BYTES_PER_NODE = {
 DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf16": "f32 (bf16 storage)"}
 # DRAM bytes per node update of the step kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the nodes of the captured
-# launch; profiles/step_kernel_mix_fp16_batched64cases.md).  Scaled to a full
-# launch by the node count.  Kept only for the kernel that was captured.
-TRAFFIC_B_PER_NODE = {"mix_fp16": 90.27}
+# launch; profiles/step_kernel_fp32_batched64cases.md).  Scaled to a full
+# launch by the node count.  Kept only for the kernel build that was captured.
+TRAFFIC_B_PER_NODE = {"fp32": 159.45}
 
 
 def dist_env():
@@ -302,8 +303,11 @@ def run_cuda(args):
         line["e2e"] = e2e(cases, args, torch)
     if rank == 0 and not args.no_extra:
         sim.close()
-        if args.workload == "batched" and prec != "fp32":
-            line["batched_fp32"] = batched_other(torch, args, "fp32")
+        if args.workload == "batched":
+            for other in ("fp32", "mix_fp16", "fp64"):
+                if other != prec:
+                    line[f"batched_{other}"] = batched_other(torch, args, other, steps=args.steps if other != "fp64"
+                                                             else max(3, args.steps // 5))
         line["single_case_fp32"] = single_case(torch, "oscillating", "fp32", args.steps)
         line["single_case_fp64"] = single_case(torch, "oscillating", "fp64", max(4, args.steps // 4))
     if rank == 0 and not args.no_cpu:
@@ -345,7 +349,7 @@ def e2e(cases, args, torch):
             "d2h_bytes_per_step": 88}
 
 
-def batched_other(torch, args, prec):
+def batched_other(torch, args, prec, steps):
     """The same batched case set in another precision (same timing method)."""
     from paper_1810_09299_gb300 import lbm
     cases = build_cases("batched", prec, 0, args.cases)
@@ -356,7 +360,7 @@ def batched_other(torch, args, prec):
     variant = sim.autotune(reps=2)
     for _ in range(args.warmup):
         sim.step(1)
-    times = time_steps(sim, torch, args.steps)
+    times = time_steps(sim, torch, steps)
     ms = float(np.mean(times))
     peak, kind = measured_peaks()
     ach = BYTES_PER_NODE[prec] * nodes / (ms * 1e-3) / 1e9
@@ -394,7 +398,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--workload", default="batched", choices=["batched", "oscillating", "static"])
-    ap.add_argument("--precision", default="mix_fp16", choices=["fp64", "fp32", "mix_fp16", "mix_bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "mix_fp16", "mix_bf16"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -218,6 +218,15 @@ int64_t lbm_kernel_launches(const lbm_handle* h);
 int lbm_diag_reduce_noalloc(const double* d_fields, int32_t nz, int32_t nr, int32_t z_periodic, double step,
                             double* d_out, void* stream);
 
+/* Self-test of the library's bounded device waits (no paper counterpart):
+ * launches a kernel whose mbarrier phase can never complete and whose wait
+ * therefore gives up after `tries` polls, writing 1 to the device int
+ * *device_status_word (device memory, caller-owned, should hold 0 on entry).
+ * Returns LBM_ERR_TIMEOUT when the wait gave up as designed, LBM_OK if it did
+ * not, LBM_ERR_INVALID_ARG for tries < 1 or a NULL pointer.  Synchronises
+ * `stream`.  The context stays usable: the kernel leaves no work in flight. */
+int lbm_selftest_bounded_wait(int32_t tries, void* stream, int32_t* device_status_word);
+
 /* Release every resource of the handle (NULL is ignored). */
 int lbm_destroy(lbm_handle* h);
 

@@ -6,6 +6,7 @@
 #include <mutex>
 
 #include "../../include/lbm.h"
+#include "lbm_device.cuh"
 #include "lbm_internal.h"
 
 namespace axilbm {
@@ -222,6 +223,33 @@ cudaError_t launch_shape(int shape, const double* args, int nargs, int nz, int n
 }
 
 }  // namespace axilbm
+
+// ---------------------------------------------------------------- bounded-wait self-test
+namespace {
+// An mbarrier expecting two arrivals gets one, so its phase never completes:
+// the bounded wait must give up after `tries` polls and raise the status word.
+__global__ void selftest_wait_kernel(int tries, int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) axilbm::mbar_init(&bar, 2);
+    __syncthreads();
+    if (threadIdx.x == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(axilbm::smem_addr(&bar)) : "memory");
+    axilbm::mbar_wait_bounded(&bar, 0, status, tries);
+}
+}  // namespace
+
+extern "C" int lbm_selftest_bounded_wait(int32_t tries, void* stream, int32_t* device_status_word) {
+    if (tries < 1 || !device_status_word) return LBM_ERR_INVALID_ARG;
+    selftest_wait_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(tries, device_status_word);
+    if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
+    int st = 0;
+    if (cudaMemcpyAsync(&st, device_status_word, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    return st != 0 ? LBM_ERR_TIMEOUT : LBM_OK;
+}
 
 // ---------------------------------------------------------------- allocation-free reduction
 // lbm_diag_reduce_noalloc: the diagnostics reduction for callers that cannot

@@ -36,6 +36,7 @@ EXPORTS = (
     "lbm_get_state", "lbm_set_state", "lbm_checkpoint_size", "lbm_checkpoint_save",
     "lbm_checkpoint_load", "lbm_autotune", "lbm_set_variant", "lbm_num_variants",
     "lbm_kernel_launches", "lbm_destroy", "lbm_strerror", "lbm_diag_reduce_noalloc",
+    "lbm_selftest_bounded_wait",
 )
 
 
@@ -101,6 +102,7 @@ def lib():
         "lbm_destroy": (ctypes.c_int, [vp]),
         "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "lbm_diag_reduce_noalloc": (ctypes.c_int, [vp, i32, i32, i32, ctypes.c_double, vp, vp]),
+        "lbm_selftest_bounded_wait": (ctypes.c_int, [i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
