@@ -209,7 +209,8 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
                                chr_prev, p_prev);
 }
 
-// Shared-memory layout of the TMA-staged step for tile height TZ.
+// Shared-memory layout of the TMA-staged step for tile height TZ: NS stages
+// of staged inputs, one phi window, one mbarrier per stage.
 template <class Codec, int TZ>
 struct TmaTile {
     using PT = typename Codec::PT;
@@ -223,67 +224,112 @@ struct TmaTile {
     static constexpr size_t f0_bytes = (size_t)HR * HX * sizeof(F0T);
     static constexpr size_t g_bytes = (size_t)9 * TZ * kTR * sizeof(PT);
     static constexpr size_t chi_bytes = (size_t)TZ * kTR * sizeof(Real);
+    // offsets inside one stage
     static constexpr size_t off_fq = 0;
     static constexpr size_t off_f0 = al(off_fq + fq_bytes);
     static constexpr size_t off_g = al(off_f0 + f0_bytes);
     static constexpr size_t off_chz = al(off_g + g_bytes);
     static constexpr size_t off_chr = al(off_chz + chi_bytes);
-    static constexpr size_t off_phi = al(off_chr + chi_bytes);
+    static constexpr size_t stage_bytes = al(off_chr + chi_bytes);
+    // two stages when they fit comfortably, else one (FP64 with tall tiles)
+    static constexpr int NS = (2 * stage_bytes + 16384 <= 200 * 1024) ? 2 : 1;
+    static constexpr size_t off_phi = NS * stage_bytes;
     static constexpr size_t off_bar = al(off_phi + (size_t)HR * LD * sizeof(Real));
     static constexpr size_t bytes = off_bar + 128;
     static constexpr uint32_t tx_bytes = (uint32_t)(fq_bytes + f0_bytes + g_bytes + 2 * chi_bytes);
 };
 
-// The same step as step_kernel, with the tile's inputs staged in shared memory
-// by TMA tensor loads: f_0..8 over the tile plus two rows above and below and
-// eight columns either side (x stays 16-byte aligned; cells outside the arrays
-// read as zero and are never used), g and chi over the tile.  One thread issues
-// the five copies; all threads wait on one mbarrier (bounded).  The phi window
-// (Eq. 16 + ghost rules) is then computed from shared memory; only ghost cells
-// that wrap around a periodic z boundary read global memory.
+// Issue the five TMA copies of tile `tt` into one stage, completing on `bar`.
+template <class Codec, int BZ>
+__device__ __forceinline__ void tma_issue(unsigned char* stage, const TileDev& tt, const CUtensorMap* maps,
+                                          int map_set, int parity, uint64_t* bar) {
+    using L = TmaTile<Codec, BZ>;
+    const CUtensorMap* M = maps + ((size_t)tt.c * 2 + map_set) * kMapsPerCase;
+    tensormap_acquire(M + parity);
+    tensormap_acquire(M + 2 + parity);
+    tensormap_acquire(M + 4 + parity);
+    tensormap_acquire(M + 6);
+    tensormap_acquire(M + 7);
+    mbar_expect_tx(bar, L::tx_bytes);
+    tma_load_3d(stage + L::off_fq, M + parity, tt.j0 - kTmaHalo, tt.k0 - 2, 0, bar);
+    tma_load_2d(stage + L::off_f0, M + 2 + parity, tt.j0 - kTmaHalo, tt.k0 - 2, bar);
+    tma_load_3d(stage + L::off_g, M + 4 + parity, tt.j0, tt.k0, 0, bar);
+    tma_load_2d(stage + L::off_chz, M + 6, tt.j0, tt.k0, bar);
+    tma_load_2d(stage + L::off_chr, M + 7, tt.j0, tt.k0, bar);
+}
+
+// The same step as step_kernel, with each tile's inputs staged in shared
+// memory by TMA tensor loads: f_0..8 over the tile plus two rows above and
+// below and eight columns either side (x stays 16-byte aligned; cells outside
+// the arrays read as zero and are never used), g and chi over the tile.
+//
+// Persistent and pipelined: each CTA walks the tile list with stride gridDim.x;
+// while it computes tile n from one stage, the copies of tile n+1 fill the
+// other.  One thread issues the copies; every thread waits on the stage's
+// mbarrier (bounded: a timeout sets the status word, the CTA then waits
+// (bounded) for its other copies in flight and leaves).  The phi window
+// (Eq. 16 + ghost rules) is computed from shared memory; only ghost cells that
+// wrap around a periodic z boundary read global memory.
+template <class Codec, int BZ>
+constexpr int pipe_min_blocks() {
+    return (sizeof(typename Codec::Real) == 8 || BZ >= 16) ? 1 : 3;
+}
+
 template <class Codec, int BZ, bool PR>
-__global__ void __launch_bounds__(kTR * BZ, (step_min_blocks<Codec, BZ, PR>()))
-step_kernel_tma(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles, StateDev<Codec> S,
-                const CUtensorMap* __restrict__ maps, int map_set, int parity, int* __restrict__ status) {
+__global__ void __launch_bounds__(kTR * BZ, (pipe_min_blocks<Codec, BZ>()))
+step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles, int ntiles,
+                 StateDev<Codec> S, const CUtensorMap* __restrict__ maps, int map_set, int parity,
+                 int* __restrict__ status) {
     using Real = typename Codec::Real;
     using PT = typename Codec::PT;
     using F0T = typename Codec::F0T;
     using L = TmaTile<Codec, BZ>;
-    constexpr int TZ = BZ, HR = L::HR, HX = L::HX, LD = L::LD;
+    constexpr int TZ = BZ, HR = L::HR, HX = L::HX, LD = L::LD, NS = L::NS;
+    constexpr int kWaitTries = 1 << 22;
     extern __shared__ __align__(128) unsigned char smem[];
-    PT* s_fq = (PT*)(smem + L::off_fq);      // [8][HR][HX]
-    F0T* s_f0 = (F0T*)(smem + L::off_f0);    // [HR][HX]
-    PT* s_g = (PT*)(smem + L::off_g);        // [9][TZ][32]
-    Real* s_chz = (Real*)(smem + L::off_chz);  // [TZ][32]
-    Real* s_chr = (Real*)(smem + L::off_chr);
-    Real* sphi = (Real*)(smem + L::off_phi);   // [HR][LD]
+    Real* sphi = (Real*)(smem + L::off_phi);  // [HR][LD]
     uint64_t* bar = (uint64_t*)(smem + L::off_bar);
-
-    const TileDev t = tiles[blockIdx.x];
-    const CaseDev& C = cases[t.c];
-    const CaseView<Codec> V = case_view<Codec>(S, C);
     const int tid = threadIdx.y * kTR + threadIdx.x;
-    if (tid == 0) mbar_init(bar, 1);
-    __syncthreads();
+    if ((int)blockIdx.x >= ntiles) return;
     if (tid == 0) {
-        const CUtensorMap* M = maps + ((size_t)t.c * 2 + map_set) * kMapsPerCase;
-        for (int q : {parity, 2 + parity, 4 + parity, 6, 7}) tensormap_acquire(M + q);
-        mbar_expect_tx(bar, L::tx_bytes);
-        tma_load_3d(s_fq, M + parity, t.j0 - kTmaHalo, t.k0 - 2, 0, bar);
-        tma_load_2d(s_f0, M + 2 + parity, t.j0 - kTmaHalo, t.k0 - 2, bar);
-        tma_load_3d(s_g, M + 4 + parity, t.j0, t.k0, 0, bar);
-        tma_load_2d(s_chz, M + 6, t.j0, t.k0, bar);
-        tma_load_2d(s_chr, M + 7, t.j0, t.k0, bar);
+        for (int q = 0; q < NS; ++q) mbar_init(bar + q, 1);
     }
-    const bool ok = mbar_wait_bounded(bar, 0, status, 1 << 22);
-
-    // phi window from the staged populations
-    if (ok) {
+    __syncthreads();
+    if (tid == 0) tma_issue<Codec, BZ>(smem, tiles[blockIdx.x], maps, map_set, parity, bar);
+    unsigned phases = 0u;  // bit s: parity of the next phase of stage s
+    for (int n = 0, t = blockIdx.x; t < ntiles; ++n, t += gridDim.x) {
+        const int s = NS == 2 ? (n & 1) : 0;
+        unsigned char* st = smem + s * L::stage_bytes;
+        const int tn = t + gridDim.x;
+        if (NS == 2 && tid == 0 && tn < ntiles) {
+            // the other stage was last read before the barrier that closed the
+            // previous iteration; order those reads before the async writes
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma_issue<Codec, BZ>(smem + (s ^ 1) * L::stage_bytes, tiles[tn], maps, map_set, parity, bar + (s ^ 1));
+        }
+        const bool ok = __syncthreads_and(mbar_wait_bounded(bar + s, (phases >> s) & 1u, status, kWaitTries));
+        phases ^= 1u << s;
+        if (!ok) {
+            // give the copies still in flight a bounded chance to land, then leave
+            if (NS == 2 && tid == 0 && tn < ntiles)
+                mbar_wait_bounded(bar + (s ^ 1), (phases >> (s ^ 1)) & 1u, status, kWaitTries);
+            __syncthreads();
+            return;
+        }
+        const TileDev tt = tiles[t];
+        const CaseDev& C = cases[tt.c];
+        const CaseView<Codec> V = case_view<Codec>(S, C);
+        const PT* s_fq = (const PT*)(st + L::off_fq);      // [8][HR][HX]
+        const F0T* s_f0 = (const F0T*)(st + L::off_f0);    // [HR][HX]
+        const PT* s_g = (const PT*)(st + L::off_g);        // [9][TZ][32]
+        const Real* s_chz = (const Real*)(st + L::off_chz);
+        const Real* s_chr = (const Real*)(st + L::off_chr);
+        // phi window from the staged populations
         for (int idx = tid; idx < HR * LD; idx += kTR * BZ) {
             const int a = idx / LD, b = idx - (idx / LD) * LD;
-            const int km = ghost_z(t.k0 - 2 + a, C.nz, C.zper);
-            const int jm = ghost_r(t.j0 - 2 + b, C.nr);
-            const int sa = km - (t.k0 - 2), sx = jm - (t.j0 - kTmaHalo);
+            const int km = ghost_z(tt.k0 - 2 + a, C.nz, C.zper);
+            const int jm = ghost_r(tt.j0 - 2 + b, C.nr);
+            const int sa = km - (tt.k0 - 2), sx = jm - (tt.j0 - kTmaHalo);
             const Real r = (Real)jm + (Real)0.5;
             Real phi;
             if (sa >= 0 && sa < HR && sx >= 0 && sx < HX) {
@@ -297,24 +343,31 @@ step_kernel_tma(const CaseDev* __restrict__ cases, const TileDev* __restrict__ t
             }
             sphi[idx] = phi;
         }
+        __syncthreads();
+        const int j = tt.j0 + threadIdx.x;
+        const int k = tt.k0 + threadIdx.y;
+        if (j < C.nr && k < C.nz) {
+            const int loc = k * C.pitch + j;
+            const int o = (threadIdx.y + 2) * HX + threadIdx.x + kTmaHalo;
+            const F0T f0raw = s_f0[o];
+            PT fraw[8], graw[9];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) fraw[i - 1] = s_fq[(i - 1) * HR * HX + o];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) graw[i] = s_g[(i * TZ + threadIdx.y) * kTR + threadIdx.x];
+            const Real chz_prev = s_chz[threadIdx.y * kTR + threadIdx.x];
+            const Real chr_prev = s_chr[threadIdx.y * kTR + threadIdx.x];
+            const Real p_prev = C.p_coupling == 1 ? V.p_prev[loc] : (Real)0;
+            node_update<Codec, PR, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw, graw,
+                                       chz_prev, chr_prev, p_prev);
+        }
+        // every read of this stage and of the phi window is done before either is refilled
+        __syncthreads();
+        if (NS == 1 && tid == 0 && tn < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma_issue<Codec, BZ>(smem, tiles[tn], maps, map_set, parity, bar);
+        }
     }
-    __syncthreads();
-    const int j = t.j0 + threadIdx.x;
-    const int k = t.k0 + threadIdx.y;
-    if (!ok || j >= C.nr || k >= C.nz) return;
-    const int loc = k * C.pitch + j;
-    const int o = (threadIdx.y + 2) * HX + threadIdx.x + kTmaHalo;
-    const F0T f0raw = s_f0[o];
-    PT fraw[8], graw[9];
-#pragma unroll
-    for (int i = 1; i < 9; ++i) fraw[i - 1] = s_fq[(i - 1) * HR * HX + o];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) graw[i] = s_g[(i * TZ + threadIdx.y) * kTR + threadIdx.x];
-    const Real chz_prev = s_chz[threadIdx.y * kTR + threadIdx.x];
-    const Real chr_prev = s_chr[threadIdx.y * kTR + threadIdx.x];
-    const Real p_prev = C.p_coupling == 1 ? V.p_prev[loc] : (Real)0;
-    node_update<Codec, PR, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw, graw, chz_prev,
-                               chr_prev, p_prev);
 }
 
 // phi, rho, u_z, u_r, p of one case into dense FP64 arrays out[5][nz][nr].
@@ -494,17 +547,24 @@ StateDev<Codec> make_state(const DeviceState& D, int parity) {
     return S;
 }
 
+// Persistent grid for the pipelined kernel: as many CTAs as fit on the GPU at
+// once (queried per instantiation), capped by the tile count.
 template <class Codec, int BZ, bool PR>
 void launch_tma(int ntiles, cudaStream_t st, const CaseDev* cs, const TileDev* tiles, const StateDev<Codec>& S,
                 const DeviceState& D, int parity) {
     using L = TmaTile<Codec, BZ>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(step_kernel_tma<Codec, BZ, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
-        attr_set = true;
+    static int grid_cap = 0;
+    if (grid_cap == 0) {
+        cudaFuncSetAttribute(step_kernel_pipe<Codec, BZ, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel_pipe<Codec, BZ, PR>, kTR * BZ, L::bytes);
+        grid_cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
     }
-    step_kernel_tma<Codec, BZ, PR><<<ntiles, dim3(kTR, BZ), L::bytes, st>>>(
-        cs, tiles, S, (const CUtensorMap*)D.tmaps, BZ == 8 ? 0 : 1, parity, D.status);
+    const int grid = ntiles < grid_cap ? ntiles : grid_cap;
+    step_kernel_pipe<Codec, BZ, PR><<<grid, dim3(kTR, BZ), L::bytes, st>>>(
+        cs, tiles, ntiles, S, (const CUtensorMap*)D.tmaps, BZ == 8 ? 0 : 1, parity, D.status);
 }
 
 template <class Codec, bool PR>
