@@ -306,10 +306,10 @@ def run_cuda(args):
         if args.workload == "batched":
             for other in ("fp32", "mix_fp16", "fp64"):
                 if other != prec:
-                    line[f"batched_{other}"] = batched_other(torch, args, other, steps=args.steps if other != "fp64"
-                                                             else max(3, args.steps // 5))
-        line["single_case_fp32"] = single_case(torch, "oscillating", "fp32", args.steps)
-        line["single_case_fp64"] = single_case(torch, "oscillating", "fp64", max(4, args.steps // 4))
+                    line[f"batched_{other}"] = batched_other(torch, args, other, steps=min(args.steps, 50)
+                                                             if other != "fp64" else 5)
+        line["single_case_fp32"] = single_case(torch, "oscillating", "fp32", min(args.steps, 50))
+        line["single_case_fp64"] = single_case(torch, "oscillating", "fp64", min(max(4, args.steps // 4), 20))
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(cases[0], budget_s=args.cpu_seconds)
     if rank == 0:
@@ -394,7 +394,7 @@ def single_case(torch, workload, prec, steps):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--workload", default="batched", choices=["batched", "oscillating", "static"])
