@@ -146,8 +146,18 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     constexpr int LD = kTR + 4;
     constexpr int NRING = 4 * LD + 4 * TZ;
     __shared__ Real sphi[(TZ + 4) * LD];
+    // The case's parameters are copied to shared memory first: read from
+    // there, the collision's many per-case constants need no global loads.
+    __shared__ __align__(16) CaseDev sC;
+    static_assert(sizeof(CaseDev) % 4 == 0 && sizeof(CaseDev) / 4 <= kTR * BZ, "one word per thread");
     const TileDev t = tiles[blockIdx.x];
-    const CaseDev& C = cases[t.c];
+    {
+        const int q = threadIdx.y * kTR + threadIdx.x;
+        if (q < (int)(sizeof(CaseDev) / 4))
+            reinterpret_cast<int32_t*>(&sC)[q] = reinterpret_cast<const int32_t*>(cases + t.c)[q];
+    }
+    __syncthreads();
+    const CaseDev& C = sC;
     const CaseView<Codec> V = case_view<Codec>(S, C);
     const int j = t.j0 + threadIdx.x;
     const int k = t.k0 + threadIdx.y;
