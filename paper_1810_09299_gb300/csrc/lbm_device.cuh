@@ -334,6 +334,124 @@ __device__ __forceinline__ void inverse_moments(const Real* m, Real* x) {
     x[8] = d + qz - qr - a8;
 }
 
+// ---------------------------------------------------------------- paired FP32 transforms
+// The two LBEs apply the same moment matrix to their nine populations.  In
+// FP32 the pair (f_i, g_i) is held as one float2 and transformed with the
+// packed FP32x2 instructions of sm_100-family GPUs (one instruction per pair,
+// IEEE round-to-nearest per component); a - b is the exact FMA b * -1 + a.
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 p_fma(float s, float2 a, float2 b) { return __ffma2_rn(make_float2(s, s), a, b); }
+__device__ __forceinline__ float2 p_mul(float s, float2 a) { return __fmul2_rn(make_float2(s, s), a); }
+
+// Two double-float accumulators advanced together: the error-free TwoSum
+// steps of ff_add, one packed instruction per step for both lanes.
+struct FF2 {
+    float2 hi, lo;
+};
+__device__ __forceinline__ void ff2_add(FF2& a, float2 x) {
+    const float2 s = p_add(a.hi, x);
+    const float2 bb = p_sub(s, a.hi);
+    const float2 e = p_add(p_sub(a.hi, p_sub(s, bb)), p_sub(x, bb));
+    a.hi = s;
+    a.lo = p_add(a.lo, e);
+}
+// a -= x (TwoSum of a.hi and -x)
+__device__ __forceinline__ void ff2_sub(FF2& a, float2 x) {
+    const float2 s = p_sub(a.hi, x);
+    const float2 bb = p_sub(s, a.hi);
+    const float2 e = p_sub(p_sub(a.hi, p_sub(s, bb)), p_add(x, bb));
+    a.hi = s;
+    a.lo = p_add(a.lo, e);
+}
+// The sum of both lanes as one normalised double-float.
+__device__ __forceinline__ FF ff2_merge(const FF2& a) {
+    FF r{a.hi.x, a.lo.x + a.lo.y};
+    ff_add(r, a.hi.y);
+    return ff_norm(r);
+}
+
+// M x for a pair of population sets (the rows of moments()).
+__device__ __forceinline__ void moments_p(const float2* x, float2* m) {
+    const float2 s13 = p_add(x[1], x[3]), s24 = p_add(x[2], x[4]);
+    const float2 s57 = p_add(x[5], x[7]), s68 = p_add(x[6], x[8]);
+    const float2 a14 = p_add(s13, s24), a58 = p_add(s57, s68);
+    m[0] = p_add(p_add(x[0], a14), a58);
+    m[1] = p_fma(-4.0f, x[0], p_sub(p_add(a58, a58), a14));
+    m[2] = p_fma(4.0f, x[0], p_fma(-2.0f, a14, a58));
+    const float2 d13 = p_sub(x[1], x[3]), d24 = p_sub(x[2], x[4]);
+    const float2 d57 = p_sub(x[5], x[7]), d68 = p_sub(x[6], x[8]);
+    const float2 e = p_sub(d57, d68), o = p_add(d57, d68);
+    m[3] = p_add(d13, e);
+    m[4] = p_fma(-2.0f, d13, e);
+    m[5] = p_add(d24, o);
+    m[6] = p_fma(-2.0f, d24, o);
+    m[7] = p_sub(s13, s24);
+    m[8] = p_sub(s57, s68);
+}
+
+// M^-1 m for a pair of moment sets (the algebra of inverse_moments()).
+__device__ __forceinline__ void inverse_moments_p(const float2* m, float2* x) {
+    const float2 a0 = p_mul(1.0f / 9.0f, m[0]);
+    const float2 a1 = p_mul(1.0f / 36.0f, m[1]);
+    const float2 a2 = p_mul(1.0f / 36.0f, m[2]);
+    const float2 a3 = p_mul(1.0f / 6.0f, m[3]);
+    const float2 a4 = p_mul(1.0f / 12.0f, m[4]);
+    const float2 a5 = p_mul(1.0f / 6.0f, m[5]);
+    const float2 a6 = p_mul(1.0f / 12.0f, m[6]);
+    const float2 a7 = p_mul(0.25f, m[7]);
+    const float2 a8 = p_mul(0.25f, m[8]);
+    const float2 e = p_fma(-2.0f, a2, p_sub(a0, a1));  // axis directions, isotropic part
+    const float2 d = p_fma(2.0f, a1, p_add(a0, a2));   // diagonal directions, isotropic part
+    const float2 jz = p_fma(-2.0f, a4, a3), jr = p_fma(-2.0f, a6, a5);
+    const float2 qz = p_add(a3, a4), qr = p_add(a5, a6);
+    const float2 qp = p_add(qz, qr), qm = p_sub(qz, qr);
+    x[0] = p_fma(-4.0f, a1, p_fma(4.0f, a2, a0));
+    const float2 ep = p_add(e, a7), em = p_sub(e, a7);
+    x[1] = p_add(ep, jz);
+    x[3] = p_sub(ep, jz);
+    x[2] = p_add(em, jr);
+    x[4] = p_sub(em, jr);
+    const float2 dp = p_add(d, a8), dm = p_sub(d, a8);
+    x[5] = p_add(dp, qp);
+    x[7] = p_sub(dp, qp);
+    x[6] = p_sub(dm, qm);
+    x[8] = p_add(dm, qm);
+}
+
+// mf = M f and mg = M g: one packed transform in FP32, two scalar ones in FP64.
+__device__ __forceinline__ void moments_fg(const double* f, const double* g, double* mf, double* mg) {
+    moments<double>(f, mf);
+    moments<double>(g, mg);
+}
+__device__ __forceinline__ void moments_fg(const float* f, const float* g, float* mf, float* mg) {
+    float2 x[9], m[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) x[i] = make_float2(f[i], g[i]);
+    moments_p(x, m);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        mf[i] = m[i].x;
+        mg[i] = m[i].y;
+    }
+}
+// f+ = M^-1 mf+ and g+ = M^-1 mg+.
+__device__ __forceinline__ void inverse_moments_fg(const double* mf, const double* mg, double* f, double* g) {
+    inverse_moments<double>(mf, f);
+    inverse_moments<double>(mg, g);
+}
+__device__ __forceinline__ void inverse_moments_fg(const float* mf, const float* mg, float* f, float* g) {
+    float2 m[9], x[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) m[i] = make_float2(mf[i], mg[i]);
+    inverse_moments_p(m, x);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        f[i] = x[i].x;
+        g[i] = x[i].y;
+    }
+}
+
 // Everything before the collisions for node (k, j) of case C, from the
 // shared phi window (centred on (a, b)) and the node's decoded g.
 //
@@ -342,8 +460,8 @@ __device__ __forceinline__ void inverse_moments(const Real* m, Real* x) {
 // 1/tau_g(x) -- is known at compile time, so unit-rate moments go straight to
 // their equilibrium and s_p = (s1 + s2 - s1 s2) / (2 s1 s2) = tau_g / 2.
 template <typename Real, int LD, bool PR = false>
-__device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, int a, int b, int j, const Real* g,
-                                            Real p_prev, Macro<Real>& m) {
+__device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, int a, int b, int j, const Real* mg,
+                                            Real g0, Real p_prev, Macro<Real>& m) {
     const CaseReal<Real>& P = case_params<Real>(C);
     m.r = (Real)j + (Real)0.5;
     m.inv_r = rcp_(m.r);
@@ -371,9 +489,10 @@ __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, 
     m.nzn = m.gz * ign;
     m.nrn = m.gr * ign;
     m.lam = (Real)4 * m.phi * ((Real)1 - m.phi) * P.inv_W;
-    // hydrodynamic moments
-    moments<Real>(g, m.mg);
-    const Real Jz = m.mg[3], Jr = m.mg[5], S0 = m.mg[0] - g[0];
+    // hydrodynamic moments (M g, computed by the caller)
+#pragma unroll
+    for (int i = 0; i < 9; ++i) m.mg[i] = mg[i];
+    const Real Jz = m.mg[3], Jr = m.mg[5], S0 = m.mg[0] - g0;
     const Real drho = rho_l - rho_g;
     const Real dzrho = drho * m.gz, drrho = drho * m.gr;
     Real sp;
@@ -416,11 +535,9 @@ __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, 
 // Phase field (Eq. 19 in moment space with Eq. 21-23).  chi = (r phi u_z,
 // r phi u_r + M phi); the time derivative of Eq. 38 uses chi^{n-1}.
 template <typename Real, bool PR = false>
-__device__ __forceinline__ void collide_f(const CaseDev& C, const Macro<Real>& m, const Real* f, Real chi_z_prev,
-                                          Real chi_r_prev, Real& chi_z, Real& chi_r, Real* fpost) {
+__device__ __forceinline__ void collide_f(const CaseDev& C, const Macro<Real>& m, const Real* mf, Real chi_z_prev,
+                                          Real chi_r_prev, Real& chi_z, Real& chi_r, Real* mp) {
     const CaseReal<Real>& P = case_params<Real>(C);
-    Real mf[9];
-    moments<Real>(f, mf);
     const Real rphi = mf[0];  // = r phi exactly (phi is sum f / r)
     chi_z = m.r * m.phi * m.uz;
     chi_r = m.r * m.phi * m.ur + P.mob * m.phi;
@@ -428,7 +545,6 @@ __device__ __forceinline__ void collide_f(const CaseDev& C, const Macro<Real>& m
     const Real mR2 = (chi_r - chi_r_prev) + m.r * m.nrn * m.lam * (Real)(1.0 / 3.0);
     const Real meq[9] = {rphi, (Real)-2 * rphi, rphi, chi_z, -chi_z, chi_r, -chi_r, (Real)0, (Real)0};
     const Real mR[9] = {(Real)0, (Real)0, (Real)0, mR1, -mR1, mR2, -mR2, (Real)0, (Real)0};
-    Real mp[9];
     if constexpr (PR) {
         // unit rates: m0 is conserved, m1, m2, m7, m8 take their equilibria
         const Real s = P.sf[3], h = (Real)1 - (Real)0.5 * s;
@@ -446,12 +562,11 @@ __device__ __forceinline__ void collide_f(const CaseDev& C, const Macro<Real>& m
             mp[k] = mf[k] - s * (mf[k] - meq[k]) + ((Real)1 - (Real)0.5 * s) * mR[k];
         }
     }
-    inverse_moments<Real>(mp, fpost);
 }
 
 // Hydrodynamics (Eq. 24 in moment space with Eq. 36-37).
 template <typename Real, bool PR = false>
-__device__ __forceinline__ void collide_g(const CaseDev& C, const Macro<Real>& m, Real* gpost) {
+__device__ __forceinline__ void collide_g(const CaseDev& C, const Macro<Real>& m, Real* mp) {
     const CaseReal<Real>& P = case_params<Real>(C);
     const Real r = m.r, rho = m.rho, uz = m.uz, ur = m.ur, p = m.p;
     const Real u2 = uz * uz + ur * ur;
@@ -472,7 +587,6 @@ __device__ __forceinline__ void collide_g(const CaseDev& C, const Macro<Real>& m
                         m.Fz, -m.Fz, m.Fr, -m.Fr,
                         (Real)(2.0 / 3.0) * (uz * dz_rr - ur * dr_rr),
                         (Real)(1.0 / 3.0) * (uz * dr_rr + ur * dz_rr)};
-    Real mp[9];
     if constexpr (PR) {
         const Real s = m.sg[1], h = (Real)1 - (Real)0.5 * s;
 #pragma unroll
@@ -487,7 +601,6 @@ __device__ __forceinline__ void collide_g(const CaseDev& C, const Macro<Real>& m
             mp[k] = m.mg[k] - s * (m.mg[k] - meq[k]) + ((Real)1 - (Real)0.5 * s) * MT[k];
         }
     }
-    inverse_moments<Real>(mp, gpost);
 }
 
 // ---------------------------------------------------------------- streaming

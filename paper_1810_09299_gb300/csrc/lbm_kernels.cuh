@@ -35,17 +35,19 @@ constexpr int step_min_blocks() {
 
 // Store one post-collision population pair (f_I, g_I) at its destination
 // (local index `dl`, direction `dir`, destination radius normalisation
-// wr / iw) and account the stored f in the mass ledger.
+// wr / iw).  Returns f_I as the reader will decode it (for the mass ledger).
 template <class Codec, int I>
-__device__ __forceinline__ void store_pair(const CaseView<Codec>& V, int dl, int dir, typename Codec::Real wr,
-                                           typename Codec::Real iw, typename Codec::Real fpi,
-                                           typename Codec::Real gpi, FF& ledger) {
+__device__ __forceinline__ typename Codec::Real store_pair(const CaseView<Codec>& V, int dl, int dir,
+                                                           typename Codec::Real wr, typename Codec::Real iw,
+                                                           typename Codec::Real fpi, typename Codec::Real gpi) {
+    typename Codec::Real stored = fpi;
     if (I != 0) {
         const auto e = Codec::enc_f(fpi, wr, iw);
         V.fout(dir, dl) = e;
-        if constexpr (Codec::kLedger) ff_add(ledger, -(float)Codec::dec_f(e, wr));
+        stored = Codec::dec_f(e, wr);
     }
     V.gout(dir, dl) = Codec::enc_g(gpi, wr, iw);
+    return stored;
 }
 
 // Steps a4-a10 for one node whose raw stored values have been fetched: decode,
@@ -65,21 +67,28 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     Real g[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) g[i] = Codec::dec_g(graw[i], (Real)w_of(i) * r);
+    Real mf[9], mg[9];
+    moments_fg(f, g, mf, mg);
     Macro<Real> m;
-    node_macros<Real, LD, PR>(C, sphi, a, b, j, g, p_prev, m);
-    FF ledger{0.0f, 0.0f};
+    node_macros<Real, LD, PR>(C, sphi, a, b, j, mg, g[0], p_prev, m);
+    // mass ledger: two double-float lanes (f_0 and f_1..4; f_5..8) advanced
+    // together; incoming total first, exact
+    FF2 ledger{};
     if constexpr (Codec::kLedger) {
-        ledger = FF{((const float2&)f0raw).x, ((const float2&)f0raw).y};
+        ledger = FF2{make_float2(((const float2&)f0raw).x, 0.0f), make_float2(((const float2&)f0raw).y, 0.0f)};
 #pragma unroll
-        for (int i = 1; i < 9; ++i) ff_add(ledger, (float)f[i]);  // incoming total, exact
+        for (int i = 1; i < 5; ++i) ff2_add(ledger, make_float2((float)f[i], (float)f[i + 4]));
     }
-    Real fp[9], chz, chr;
-    collide_f<Real, PR>(C, m, f, chz_prev, chr_prev, chz, chr, fp);
+    Real mpf[9], chz, chr;
+    collide_f<Real, PR>(C, m, mf, chz_prev, chr_prev, chz, chr, mpf);
     V.chi_z[loc] = chz;
     V.chi_r[loc] = chr;
     if (C.p_coupling == 1) V.p_prev[loc] = m.p;
-    Real gp[9];
-    collide_g<Real, PR>(C, m, gp);
+    Real mpg[9];
+    collide_g<Real, PR>(C, m, mpg);
+    Real fp[9], gp[9];
+    inverse_moments_fg(mpf, mpg, fp, gp);
+    Real fs[9];  // f+ as stored, decoded
 
     // 5. streaming (Eq. 20).  Rows j-1, j, j+1 are the only destinations, so
     //    three radii serve every normalisation.
@@ -88,9 +97,9 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     const bool interior = (j >= 1) && (j + 1 < C.nr) && (k >= 1) && (k + 1 < C.nz);
     if (interior) {
         // every link lands on a neighbour inside the domain
-#define AXILBM_PUSH_FAST(I)                                                                              \
-    store_pair<Codec, I>(V, loc + cz_of(I) * C.pitch + cr_of(I), I, (Real)w_of(I) * rdst[cr_of(I) + 1],  \
-                         (Real)(1.0 / w_of(I)) * rinv[cr_of(I) + 1], fp[I], gp[I], ledger);
+#define AXILBM_PUSH_FAST(I)                                                                                    \
+    fs[I] = store_pair<Codec, I>(V, loc + cz_of(I) * C.pitch + cr_of(I), I, (Real)w_of(I) * rdst[cr_of(I) + 1], \
+                                 (Real)(1.0 / w_of(I)) * rinv[cr_of(I) + 1], fp[I], gp[I]);
         AXILBM_PUSH_FAST(0)
         AXILBM_PUSH_FAST(1)
         AXILBM_PUSH_FAST(2)
@@ -107,8 +116,8 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     {                                                                                                      \
         const Dest d = destination<I>(k, j, C.nr, C.nz, C.zper);                                           \
         const int s = d.j - j + 1;                                                                         \
-        store_pair<Codec, I>(V, d.k * C.pitch + d.j, d.dir, (Real)w_of(I) * rdst[s],                       \
-                             (Real)(1.0 / w_of(I)) * rinv[s], fp[I], gp[I], ledger);                       \
+        fs[I] = store_pair<Codec, I>(V, d.k * C.pitch + d.j, d.dir, (Real)w_of(I) * rdst[s],               \
+                                     (Real)(1.0 / w_of(I)) * rinv[s], fp[I], gp[I]);                       \
     }
         AXILBM_PUSH(0)
         AXILBM_PUSH(1)
@@ -124,7 +133,9 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     // f_0: the collision's value (FP64), or the mass ledger: incoming total
     // minus the outgoing f_1..8 as they will be read back
     if constexpr (Codec::kLedger) {
-        const FF l = ff_norm(ledger);
+#pragma unroll
+        for (int i = 1; i < 5; ++i) ff2_sub(ledger, make_float2((float)fs[i], (float)fs[i + 4]));
+        const FF l = ff2_merge(ledger);
         V.f0_out[loc] = make_float2(l.hi, l.lo);
     } else {
         V.f0_out[loc] = fp[0];
@@ -403,8 +414,10 @@ fields_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ til
 #pragma unroll
     for (int i = 0; i < 9; ++i) g[i] = Codec::dec_g(V.gin(i, loc), (Real)w_of(i) * r);
     Macro<Real> m;
-    node_macros<Real, LD>(C, sphi, threadIdx.y + 2, threadIdx.x + 2, j, g, C.p_coupling == 1 ? V.p_prev[loc] : (Real)0,
-                          m);
+    Real mg[9];
+    moments<Real>(g, mg);
+    node_macros<Real, LD>(C, sphi, threadIdx.y + 2, threadIdx.x + 2, j, mg, g[0],
+                          C.p_coupling == 1 ? V.p_prev[loc] : (Real)0, m);
     const int64_t n = (int64_t)C.nz * C.nr, o = (int64_t)k * C.nr + j;
     out[o] = (double)m.phi;
     out[n + o] = (double)m.rho;
