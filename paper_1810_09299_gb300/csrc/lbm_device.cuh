@@ -63,7 +63,9 @@ struct CaseDev {
     int32_t pad1;
     CaseReal<double> pd;
     CaseReal<float> pf;
+    int32_t pad2[2];    // size a multiple of 16 bytes (bulk-copyable)
 };
+static_assert(sizeof(CaseDev) % 16 == 0, "CaseDev is copied to shared memory by a bulk copy");
 
 template <typename Real>
 __device__ __forceinline__ const CaseReal<Real>& case_params(const CaseDev& C);
@@ -684,6 +686,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         "[%5];" ::"r"(smem_addr(dst)),
         "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
         : "memory");
+}
+
+// Plain bulk copy global -> shared (no tensor map): both addresses 16-byte
+// aligned, `bytes` a multiple of 16; completes on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"((uint64_t)src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
 }
 
 }  // namespace axilbm

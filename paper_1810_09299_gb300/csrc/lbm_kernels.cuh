@@ -230,8 +230,13 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
                                chr_prev, p_prev);
 }
 
-// Shared-memory layout of the TMA-staged step for tile height TZ: NS stages
-// of staged inputs, one phi window, one mbarrier per stage.
+// Shared-memory layout of one stage of the TMA-pipelined step for tile
+// height TZ, then the phi window and one mbarrier per stage.  A stage holds
+// its tile's record, the record of the tile after it in the CTA's walk, the
+// tile's case record and the tile's inputs:
+//   f_1..8, f_0 over rows k0-2 .. k0+TZ+1 and columns j0-8 .. j0+39 (the ring
+//   of the phi window lies inside; x stays 16-byte aligned; cells outside the
+//   arrays read as zero and are never used), g_0..8 and chi over the tile.
 template <class Codec, int TZ>
 struct TmaTile {
     using PT = typename Codec::PT;
@@ -246,32 +251,42 @@ struct TmaTile {
     static constexpr size_t g_bytes = (size_t)9 * TZ * kTR * sizeof(PT);
     static constexpr size_t chi_bytes = (size_t)TZ * kTR * sizeof(Real);
     // offsets inside one stage
-    static constexpr size_t off_fq = 0;
+    static constexpr size_t off_rec = 0;                   // TileDev of this stage's tile
+    static constexpr size_t off_next = 16;                 // TileDev of the CTA's next tile after it
+    static constexpr size_t off_case = 32;                 // CaseDev of the tile's case
+    static constexpr size_t off_fq = al(off_case + sizeof(CaseDev));
     static constexpr size_t off_f0 = al(off_fq + fq_bytes);
     static constexpr size_t off_g = al(off_f0 + f0_bytes);
     static constexpr size_t off_chz = al(off_g + g_bytes);
     static constexpr size_t off_chr = al(off_chz + chi_bytes);
     static constexpr size_t stage_bytes = al(off_chr + chi_bytes);
-    // two stages when they fit comfortably, else one (FP64 with tall tiles)
+    // two stages when they fit, else one (FP64 with tall tiles)
     static constexpr int NS = (2 * stage_bytes + 16384 <= 200 * 1024) ? 2 : 1;
     static constexpr size_t off_phi = NS * stage_bytes;
     static constexpr size_t off_bar = al(off_phi + (size_t)HR * LD * sizeof(Real));
     static constexpr size_t bytes = off_bar + 128;
-    static constexpr uint32_t tx_bytes = (uint32_t)(fq_bytes + f0_bytes + g_bytes + 2 * chi_bytes);
+    static constexpr uint32_t tensor_bytes = (uint32_t)(fq_bytes + f0_bytes + g_bytes + 2 * chi_bytes);
 };
 
-// Issue the five TMA copies of tile `tt` into one stage, completing on `bar`.
+// Fill one stage with tile `tt` (whose successor in the CTA's walk is tile
+// index `next`): records, case record and the five tensor copies, all
+// completing on `bar`.  Called by one thread.
 template <class Codec, int BZ>
-__device__ __forceinline__ void tma_issue(unsigned char* stage, const TileDev& tt, const CUtensorMap* maps,
+__device__ __forceinline__ void tma_issue(unsigned char* stage, const TileDev tt, int next, int ntiles,
+                                          const CaseDev* cases, const TileDev* tiles, const CUtensorMap* maps,
                                           int map_set, int parity, uint64_t* bar) {
     using L = TmaTile<Codec, BZ>;
+    *(TileDev*)(stage + L::off_rec) = tt;
     const CUtensorMap* M = maps + ((size_t)tt.c * 2 + map_set) * kMapsPerCase;
     tensormap_acquire(M + parity);
     tensormap_acquire(M + 2 + parity);
     tensormap_acquire(M + 4 + parity);
     tensormap_acquire(M + 6);
     tensormap_acquire(M + 7);
-    mbar_expect_tx(bar, L::tx_bytes);
+    const bool has_next = next < ntiles;
+    mbar_expect_tx(bar, L::tensor_bytes + (uint32_t)sizeof(CaseDev) + (has_next ? (uint32_t)sizeof(TileDev) : 0u));
+    bulk_load(stage + L::off_case, cases + tt.c, (uint32_t)sizeof(CaseDev), bar);
+    if (has_next) bulk_load(stage + L::off_next, tiles + next, (uint32_t)sizeof(TileDev), bar);
     tma_load_3d(stage + L::off_fq, M + parity, tt.j0 - kTmaHalo, tt.k0 - 2, 0, bar);
     tma_load_2d(stage + L::off_f0, M + 2 + parity, tt.j0 - kTmaHalo, tt.k0 - 2, bar);
     tma_load_3d(stage + L::off_g, M + 4 + parity, tt.j0, tt.k0, 0, bar);
@@ -279,23 +294,52 @@ __device__ __forceinline__ void tma_issue(unsigned char* stage, const TileDev& t
     tma_load_2d(stage + L::off_chr, M + 7, tt.j0, tt.k0, bar);
 }
 
-// The same step as step_kernel, with each tile's inputs staged in shared
-// memory by TMA tensor loads: f_0..8 over the tile plus two rows above and
-// below and eight columns either side (x stays 16-byte aligned; cells outside
-// the arrays read as zero and are never used), g and chi over the tile.
-//
-// Persistent and pipelined: each CTA walks the tile list with stride gridDim.x;
-// while it computes tile n from one stage, the copies of tile n+1 fill the
-// other.  One thread issues the copies; every thread waits on the stage's
-// mbarrier (bounded: a timeout sets the status word, the CTA then waits
-// (bounded) for its other copies in flight and leaves).  The phi window
-// (Eq. 16 + ghost rules) is computed from shared memory; only ghost cells that
-// wrap around a periodic z boundary read global memory.
-template <class Codec, int BZ>
-constexpr int pipe_min_blocks() {
-    return (sizeof(typename Codec::Real) == 8 || BZ >= 16) ? 1 : 3;
+// phi at window cell (a, b) of tile tt (Eq. 16 + ghost rules), from the
+// staged populations when the ghost-mapped node lies in the staged box, else
+// (a periodic z wrap) from global memory.
+template <class Codec, int TZ>
+__device__ __forceinline__ typename Codec::Real staged_phi(const unsigned char* st, const CaseDev& C,
+                                                           const CaseView<Codec>& V, const TileDev& tt, int a,
+                                                           int b) {
+    using L = TmaTile<Codec, TZ>;
+    using Real = typename Codec::Real;
+    const int km = ghost_z(tt.k0 - 2 + a, C.nz, C.zper);
+    const int jm = ghost_r(tt.j0 - 2 + b, C.nr);
+    const int sa = km - (tt.k0 - 2), sx = jm - (tt.j0 - kTmaHalo);
+    const Real r = (Real)jm + (Real)0.5;
+    if (sa >= 0 && sa < L::HR && sx >= 0 && sx < L::HX) {
+        const typename Codec::PT* s_fq = (const typename Codec::PT*)(st + L::off_fq);
+        const int o = sa * L::HX + sx;
+        Real sum = (Real)f0_value(((const typename Codec::F0T*)(st + L::off_f0))[o]);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) sum += Codec::dec_f(s_fq[(i - 1) * L::HR * L::HX + o], (Real)w_of(i) * r);
+        return sum * rcp_(r);
+    }
+    return node_phi<Codec>(V, km * C.pitch + jm, r, rcp_(r));
 }
 
+// Resident CTAs per SM: as many as the stages' shared memory allows (up to
+// 227 KB per SM, 1 KB reserved per CTA), at most 3 of 256 threads (80
+// registers a thread, which the pipelined loop needs to stay clear of spills)
+// or 2 of 512; one for FP64.
+template <class Codec, int BZ>
+constexpr int pipe_min_blocks() {
+    constexpr int by_smem = (int)((227u * 1024u) / (TmaTile<Codec, BZ>::bytes + 1024u));
+    constexpr int by_regs = BZ >= 16 ? 2 : 3;
+    return sizeof(typename Codec::Real) == 8 ? 1 : (by_smem < 1 ? 1 : (by_smem < by_regs ? by_smem : by_regs));
+}
+
+// The same step as step_kernel, with each tile's inputs staged in shared
+// memory by TMA, persistent and pipelined.  Each CTA walks the tile list with
+// stride gridDim.x.  After the copies of tile n have landed, one thread issues
+// those of tile n+1 into the other stage (the tile's record came with tile
+// n's stage), so they overlap the work on tile n; no thread ever waits on a
+// global load before its tile's data is in shared memory.  Each node's own phi
+// comes from its staged populations; the ring of the phi window is summed from
+// the staged box.  Every thread waits on the stage's mbarrier with a bounded
+// number of tries.  A timeout sets the status word; the timed-out stage gets a
+// second bounded wait and the CTA leaves.  Nothing else of its own is in
+// flight then, since the next stage is issued only after a successful wait.
 template <class Codec, int BZ, bool PR>
 __global__ void __launch_bounds__(kTR * BZ, (pipe_min_blocks<Codec, BZ>()))
 step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles, int ntiles,
@@ -306,6 +350,7 @@ step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
     using F0T = typename Codec::F0T;
     using L = TmaTile<Codec, BZ>;
     constexpr int TZ = BZ, HR = L::HR, HX = L::HX, LD = L::LD, NS = L::NS;
+    constexpr int NRING = 4 * LD + 4 * TZ;
     constexpr int kWaitTries = 1 << 22;
     extern __shared__ __align__(128) unsigned char smem[];
     Real* sphi = (Real*)(smem + L::off_phi);  // [HR][LD]
@@ -316,77 +361,96 @@ step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
         for (int q = 0; q < NS; ++q) mbar_init(bar + q, 1);
     }
     __syncthreads();
-    if (tid == 0) tma_issue<Codec, BZ>(smem, tiles[blockIdx.x], maps, map_set, parity, bar);
+    if (tid == 0)
+        tma_issue<Codec, BZ>(smem, tiles[blockIdx.x], blockIdx.x + gridDim.x, ntiles, cases, tiles, maps, map_set,
+                             parity, bar);
     unsigned phases = 0u;  // bit s: parity of the next phase of stage s
     for (int n = 0, t = blockIdx.x; t < ntiles; ++n, t += gridDim.x) {
         const int s = NS == 2 ? (n & 1) : 0;
-        unsigned char* st = smem + s * L::stage_bytes;
-        const int tn = t + gridDim.x;
-        if (NS == 2 && tid == 0 && tn < ntiles) {
-            // the other stage was last read before the barrier that closed the
-            // previous iteration; order those reads before the async writes
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tma_issue<Codec, BZ>(smem + (s ^ 1) * L::stage_bytes, tiles[tn], maps, map_set, parity, bar + (s ^ 1));
-        }
-        const bool ok = __syncthreads_and(mbar_wait_bounded(bar + s, (phases >> s) & 1u, status, kWaitTries));
-        phases ^= 1u << s;
+        const unsigned char* st = smem + s * L::stage_bytes;
+        // this barrier also closes every read of the other stage and of the
+        // phi window made while working on the previous tile
+        const unsigned ph = (phases >> s) & 1u;
+        const bool ok = __syncthreads_and(mbar_wait_bounded(bar + s, ph, status, kWaitTries));
         if (!ok) {
-            // give the copies still in flight a bounded chance to land, then leave
-            if (NS == 2 && tid == 0 && tn < ntiles)
-                mbar_wait_bounded(bar + (s ^ 1), (phases >> (s ^ 1)) & 1u, status, kWaitTries);
+            // this stage's copies get a second bounded chance to land before the CTA leaves
+            if (tid == 0) mbar_wait_bounded(bar + s, ph, status, kWaitTries);
             __syncthreads();
             return;
         }
-        const TileDev tt = tiles[t];
-        const CaseDev& C = cases[tt.c];
-        const CaseView<Codec> V = case_view<Codec>(S, C);
-        const PT* s_fq = (const PT*)(st + L::off_fq);      // [8][HR][HX]
-        const F0T* s_f0 = (const F0T*)(st + L::off_f0);    // [HR][HX]
-        const PT* s_g = (const PT*)(st + L::off_g);        // [9][TZ][32]
-        const Real* s_chz = (const Real*)(st + L::off_chz);
-        const Real* s_chr = (const Real*)(st + L::off_chr);
-        // phi window from the staged populations
-        for (int idx = tid; idx < HR * LD; idx += kTR * BZ) {
-            const int a = idx / LD, b = idx - (idx / LD) * LD;
-            const int km = ghost_z(tt.k0 - 2 + a, C.nz, C.zper);
-            const int jm = ghost_r(tt.j0 - 2 + b, C.nr);
-            const int sa = km - (tt.k0 - 2), sx = jm - (tt.j0 - kTmaHalo);
-            const Real r = (Real)jm + (Real)0.5;
-            Real phi;
-            if (sa >= 0 && sa < HR && sx >= 0 && sx < HX) {
-                const int o = sa * HX + sx;
-                Real sum = (Real)f0_value(s_f0[o]);
-#pragma unroll
-                for (int i = 1; i < 9; ++i) sum += Codec::dec_f(s_fq[(i - 1) * HR * HX + o], (Real)w_of(i) * r);
-                phi = sum * rcp_(r);
-            } else {
-                phi = node_phi<Codec>(V, km * C.pitch + jm, r, rcp_(r));
-            }
-            sphi[idx] = phi;
+        phases ^= 1u << s;
+        const int tn = t + gridDim.x;
+        if (NS == 2 && tid == 0 && tn < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma_issue<Codec, BZ>(smem + (s ^ 1) * L::stage_bytes, *(const TileDev*)(st + L::off_next),
+                                 tn + gridDim.x, ntiles, cases, tiles, maps, map_set, parity, bar + (s ^ 1));
         }
-        __syncthreads();
+        const TileDev tt = *(const TileDev*)(st + L::off_rec);
+        const CaseDev& C = *(const CaseDev*)(st + L::off_case);
+        const CaseView<Codec> V = case_view<Codec>(S, C);
         const int j = tt.j0 + threadIdx.x;
         const int k = tt.k0 + threadIdx.y;
-        if (j < C.nr && k < C.nz) {
-            const int loc = k * C.pitch + j;
-            const int o = (threadIdx.y + 2) * HX + threadIdx.x + kTmaHalo;
-            const F0T f0raw = s_f0[o];
-            PT fraw[8], graw[9];
+        const bool inside = (j < C.nr) && (k < C.nz);
+        // own staged inputs
+        const int o = (threadIdx.y + 2) * HX + threadIdx.x + kTmaHalo;
+        const PT* s_fq = (const PT*)(st + L::off_fq);
+        const PT* s_g = (const PT*)(st + L::off_g);
+        F0T f0raw{};
+        PT fraw[8], graw[9];
+        Real chz_prev = (Real)0, chr_prev = (Real)0;
+        if (inside) {
+            f0raw = ((const F0T*)(st + L::off_f0))[o];
 #pragma unroll
             for (int i = 1; i < 9; ++i) fraw[i - 1] = s_fq[(i - 1) * HR * HX + o];
 #pragma unroll
             for (int i = 0; i < 9; ++i) graw[i] = s_g[(i * TZ + threadIdx.y) * kTR + threadIdx.x];
-            const Real chz_prev = s_chz[threadIdx.y * kTR + threadIdx.x];
-            const Real chr_prev = s_chr[threadIdx.y * kTR + threadIdx.x];
+            chz_prev = ((const Real*)(st + L::off_chz))[threadIdx.y * kTR + threadIdx.x];
+            chr_prev = ((const Real*)(st + L::off_chr))[threadIdx.y * kTR + threadIdx.x];
+        }
+        // the ring of the phi window, from the staged box
+        for (int q = tid; q < NRING; q += kTR * BZ) {
+            int a, b;
+            if (q < 2 * LD) {
+                a = q / LD;
+                b = q - a * LD;
+            } else if (q < 4 * LD) {
+                const int q2 = q - 2 * LD;
+                a = TZ + 2 + q2 / LD;
+                b = q2 - (q2 / LD) * LD;
+            } else {
+                const int q3 = q - 4 * LD;
+                const int c = q3 / TZ;
+                a = 2 + (q3 - c * TZ);
+                b = c < 2 ? c : kTR + c;
+            }
+            sphi[a * LD + b] = staged_phi<Codec, TZ>(st, C, V, tt, a, b);
+        }
+        // the node's own phi (Eq. 16) from its staged populations
+        const Real r = (Real)j + (Real)0.5;
+        if (inside) {
+            Real sum = (Real)f0_value(f0raw);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) sum += Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
+            sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = sum * rcp_(r);
+        } else {
+            sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] =
+                staged_phi<Codec, TZ>(st, C, V, tt, threadIdx.y + 2, threadIdx.x + 2);
+        }
+        __syncthreads();
+        if (inside) {
+            const int loc = k * C.pitch + j;
             const Real p_prev = C.p_coupling == 1 ? V.p_prev[loc] : (Real)0;
             node_update<Codec, PR, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw, graw,
                                        chz_prev, chr_prev, p_prev);
         }
-        // every read of this stage and of the phi window is done before either is refilled
-        __syncthreads();
-        if (NS == 1 && tid == 0 && tn < ntiles) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tma_issue<Codec, BZ>(smem, tiles[tn], maps, map_set, parity, bar);
+        if (NS == 1) {
+            // every read of the single stage is done before it is refilled
+            __syncthreads();
+            if (tid == 0 && tn < ntiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tma_issue<Codec, BZ>(smem, *(const TileDev*)(st + L::off_next), tn + gridDim.x, ntiles, cases,
+                                     tiles, maps, map_set, parity, bar);
+            }
         }
     }
 }
