@@ -88,6 +88,9 @@ struct lbm_sim {
     double* state = nullptr;    // [21][nz][nr]
     double* partials = nullptr;
     double* diag_out = nullptr;
+    // pinned host staging for small reads (a diagnostics record and the
+    // status word), so that they return with one synchronisation
+    double* host_small = nullptr;
     std::vector<void*> allocations;
     int parity = 0;
     int variant = 0;
@@ -249,6 +252,8 @@ int upload_tiles(lbm_sim* h, const std::vector<TileDev>& t, TileDev** out) {
 }
 
 void release(lbm_sim* h) {
+    if (h->host_small) cudaFreeHost(h->host_small);
+    h->host_small = nullptr;
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
     for (void* p : h->allocations) cudaFreeAsync(p, h->stream);
@@ -365,6 +370,11 @@ int create_impl(const lbm_params* cases, int32_t n, void* stream, lbm_handle** o
     A((void**)&h->partials, diag_partials_size() * sizeof(double));
     A((void**)&h->diag_out, 16 * sizeof(double));
     A((void**)&h->D.status, 128);
+    if (rc == LBM_OK && cudaMallocHost((void**)&h->host_small, 16 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        h->host_small = nullptr;
+        rc = LBM_ERR_OOM;
+    }
     if (rc == LBM_OK) {
         std::vector<CUtensorMap> maps;
         h->tma_ok = encode_tensor_maps(h, maps);
@@ -568,21 +578,27 @@ int lbm_case_diagnostics(lbm_handle* h, int32_t icase, lbm_diag* out) {
     if (rc != LBM_OK) return rc;
     if (check_case(h, icase) != LBM_OK || !out) return LBM_ERR_INVALID_ARG;
     if (!h->initialized[icase]) return LBM_ERR_STATE;
-    rc = check_status(h);
-    if (rc != LBM_OK) return rc;
+    // the record and the device status word come back with one synchronisation
     rc = cuda_ok(h, launch_fields_any(h, icase));
     if (rc != LBM_OK) return rc;
     const lbm_params& p = h->prm[icase];
     rc = cuda_ok(h, launch_diag(h->fields, p.nz, p.nr, p.z_periodic, (double)h->case_steps[icase], h->partials,
                                 h->diag_out, h->stream));
     if (rc != LBM_OK) return rc;
-    double buf[11];
-    rc = cuda_ok(h, cudaMemcpyAsync(buf, h->diag_out, sizeof(buf), cudaMemcpyDeviceToHost, h->stream));
+    double* buf = h->host_small;          // 11 doubles of the record
+    int* st_h = (int*)(h->host_small + 12);  // the status word
+    rc = cuda_ok(h, cudaMemcpyAsync(buf, h->diag_out, 11 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (rc != LBM_OK) return rc;
+    rc = cuda_ok(h, cudaMemcpyAsync(st_h, h->D.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     if (rc != LBM_OK) return rc;
     rc = cuda_ok(h, cudaStreamSynchronize(h->stream));
     if (rc != LBM_OK) return rc;
-    static_assert(sizeof(lbm_diag) == sizeof(buf), "diag layout");
-    std::memcpy(out, buf, sizeof(buf));
+    if (*st_h != 0) {
+        h->sticky = LBM_ERR_TIMEOUT;
+        return LBM_ERR_TIMEOUT;
+    }
+    static_assert(sizeof(lbm_diag) == 11 * sizeof(double), "diag layout");
+    std::memcpy(out, buf, sizeof(lbm_diag));
     if (out->nonfinite > 0) return fail(h, LBM_ERR_NONFINITE);
     return LBM_OK;
 }

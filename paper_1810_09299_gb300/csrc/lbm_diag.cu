@@ -96,64 +96,104 @@ __global__ void __launch_bounds__(kDiagThreads) diag_partial_kernel(const double
     }
 }
 
-// Final combination (one thread, fixed order) and the interface lengths.
-__global__ void diag_final_kernel(const double* __restrict__ F, int nz, int nr, int zper, double step,
-                                  const double* __restrict__ partials, double* __restrict__ out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    KSum acc[7] = {};
-    double umax = 0.0, pmin = INFINITY, pmax = -INFINITY, bad = 0.0;
-    for (int b = 0; b < kDiagBlocks; ++b) {
-        const double* p = partials + b * 18;
-        for (int q = 0; q < 7; ++q) acc[q].merge(KSum{p[2 * q], p[2 * q + 1]});
-        umax = fmax(umax, p[14]);
-        pmin = fmin(pmin, p[15]);
-        pmax = fmax(pmax, p[16]);
-        bad += p[17];
+// One partial record: 7 compensated sums, 3 extrema, the non-finite count.
+__device__ __forceinline__ void merge_partial(double* a, const double* b) {
+    for (int q = 0; q < 7; ++q) {
+        KSum x{a[2 * q], a[2 * q + 1]};
+        x.merge(KSum{b[2 * q], b[2 * q + 1]});
+        a[2 * q] = x.s;
+        a[2 * q + 1] = x.c;
     }
-    const double mass = acc[0].value();
-    const double zc = acc[2].value() / mass;
-    const double win = acc[4].value(), wout = acc[6].value();
-    const double dp = (win > 0 ? acc[3].value() / win : 0.0) - (wout > 0 ? acc[5].value() / wout : 0.0);
-    // half-length of the phi > 1/2 set on the axis row (linear crossings)
+    a[14] = fmax(a[14], b[14]);
+    a[15] = fmin(a[15], b[15]);
+    a[16] = fmax(a[16], b[16]);
+    a[17] += b[17];
+}
+
+// Contribution of the axis link (k, k+1) to the length of the phi > 1/2 set on
+// the axis row (linear crossing); the last link wraps when z is periodic and
+// is half a cell at a wall.
+__device__ __forceinline__ double axis_link(const double* __restrict__ F, int k, int nz, int nr, int zper) {
+    const double a = F[(int64_t)k * nr] - 0.5;
+    int kn = k + 1;
+    if (kn >= nz) {
+        if (!zper) return a > 0 ? 0.5 : 0.0;
+        kn = 0;
+    }
+    const double b = F[(int64_t)kn * nr] - 0.5;
+    if (a > 0 && b > 0) return 1.0;
+    if (a > 0 && b <= 0) return a / (a - b);
+    if (a <= 0 && b > 0) return b / (b - a);
+    return 0.0;
+}
+
+// Final combination and the interface lengths, one block of kFinalThreads.
+// Every sum runs in a fixed order (fixed-shape trees), so the result is
+// deterministic.
+constexpr int kFinalThreads = 256;
+static_assert(kDiagBlocks <= 2 * kFinalThreads, "one fold into the first kFinalThreads partials");
+__global__ void __launch_bounds__(kFinalThreads) diag_final_kernel(const double* __restrict__ F, int nz, int nr,
+                                                                   int zper, double step,
+                                                                   const double* __restrict__ partials,
+                                                                   double* __restrict__ out) {
+    __shared__ double sp[kDiagBlocks][18];
+    __shared__ double slen[kFinalThreads];
+    __shared__ int sjmin;
+    const int t = threadIdx.x;
+    for (int i = t; i < kDiagBlocks * 18; i += kFinalThreads) (&sp[0][0])[i] = partials[i];
+    if (t == 0) sjmin = nr;
+    __syncthreads();
+    // partial records: fold kDiagBlocks into kFinalThreads, then a halving tree
+    if (t + kFinalThreads < kDiagBlocks) merge_partial(sp[t], sp[t + kFinalThreads]);
+    __syncthreads();
+    for (int stride = kFinalThreads / 2; stride > 0; stride >>= 1) {
+        if (t < stride) merge_partial(sp[t], sp[t + stride]);
+        __syncthreads();
+    }
+    // axis half-length: per-thread sums over k = t, t + T, ... then a halving tree
     double len = 0.0;
-    for (int k = 0; k < nz; ++k) {
-        const double a = F[(int64_t)k * nr] - 0.5;
-        int kn = k + 1;
-        if (kn >= nz) {
-            if (!zper) {
-                if (a > 0) len += 0.5;
-                break;
-            }
-            kn = 0;
-        }
-        const double b = F[(int64_t)kn * nr] - 0.5;
-        if (a > 0 && b > 0) len += 1.0;
-        else if (a > 0 && b <= 0) len += a / (a - b);
-        else if (a <= 0 && b > 0) len += b / (b - a);
+    for (int k = t; k < nz; k += kFinalThreads) len += axis_link(F, k, nz, nr, zper);
+    slen[t] = len;
+    __syncthreads();
+    for (int stride = kFinalThreads / 2; stride > 0; stride >>= 1) {
+        if (t < stride) slen[t] += slen[t + stride];
+        __syncthreads();
     }
-    if (!zper && F[0] - 0.5 > 0) len += 0.5;
-    // radial crossing on the row nearest the centroid
+    const double mass = KSum{sp[0][0], sp[0][1]}.value();
+    const double zc = KSum{sp[0][4], sp[0][5]}.value() / mass;
+    // radial crossing on the row nearest the centroid: the first outward crossing
     int kc = (int)floor(zc);
     kc = kc < 0 ? 0 : (kc >= nz ? nz - 1 : kc);
-    double rc = 0.0;
-    for (int j = 0; j + 1 < nr; ++j) {
+    for (int j = t; j + 1 < nr; j += kFinalThreads) {
         const double a = F[(int64_t)kc * nr + j] - 0.5, b = F[(int64_t)kc * nr + j + 1] - 0.5;
         if (a > 0 && b <= 0) {
-            rc = (j + 0.5) + a / (a - b);
+            atomicMin(&sjmin, j);
             break;
         }
     }
+    __syncthreads();
+    if (t != 0) return;
+    double rc = 0.0;
+    if (sjmin + 1 < nr) {
+        const double a = F[(int64_t)kc * nr + sjmin] - 0.5, b = F[(int64_t)kc * nr + sjmin + 1] - 0.5;
+        rc = (sjmin + 0.5) + a / (a - b);
+    }
+    double axis = slen[0];
+    if (!zper && F[0] - 0.5 > 0) axis += 0.5;
+    const double win = KSum{sp[0][8], sp[0][9]}.value(), wout = KSum{sp[0][12], sp[0][13]}.value();
+    const double dp = (win > 0 ? KSum{sp[0][6], sp[0][7]}.value() / win : 0.0) -
+                      (wout > 0 ? KSum{sp[0][10], sp[0][11]}.value() / wout : 0.0);
     out[0] = step;
     out[1] = mass;
-    out[2] = acc[1].value();
+    out[2] = KSum{sp[0][2], sp[0][3]}.value();
     out[3] = zc;
     out[4] = dp;
-    out[5] = umax;
-    out[6] = pmin;
-    out[7] = pmax;
-    out[8] = 0.5 * len;
+    out[5] = sp[0][14];
+    out[6] = sp[0][15];
+    out[7] = sp[0][16];
+    out[8] = 0.5 * axis;
     out[9] = rc;
-    out[10] = bad;
+    out[10] = sp[0][17];
 }
 
 // ---------------------------------------------------------------- shapes
@@ -210,7 +250,7 @@ int diag_partials_size() { return kDiagPartials; }
 cudaError_t launch_diag(const double* fields, int nz, int nr, int zper, double step, double* partials, double* out,
                         cudaStream_t st) {
     diag_partial_kernel<<<kDiagBlocks, kDiagThreads, 0, st>>>(fields, nz, nr, partials);
-    diag_final_kernel<<<1, 32, 0, st>>>(fields, nz, nr, zper, step, partials, out);
+    diag_final_kernel<<<1, kFinalThreads, 0, st>>>(fields, nz, nr, zper, step, partials, out);
     return cudaGetLastError();
 }
 
