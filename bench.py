@@ -48,6 +48,12 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf
 # launch; profiles/step_kernel_fp32_batched64cases.md).  Scaled to a full
 # launch by the node count.  Kept only for the kernel build that was captured.
 TRAFFIC_B_PER_NODE = {"fp32": 159.39}
+# The FP64 step is bound by the FP64 pipe, not by HBM: FP64-pipe thread
+# instructions (DADD + DFMA + DMUL) per node update from one ncu capture
+# (profiles/step_kernel_fp64_batched64cases.md), against the pipe's peak of
+# 2 per SM per cycle x 152 SMs x 2.07 GHz (maximum SM clock).
+FP64_OPS_PER_NODE = 403.3
+FP64_PIPE_PEAK_GOPS = 2 * 152 * 2.07
 # What the GPU parity tests hold each precision to against the FP64 oracle.
 PARITY_TOL = {
     "fp64": "phi, rho, u, p within 1e-11 (relative max-norm) of the FP64 oracle",
@@ -376,9 +382,15 @@ def batched_other(torch, args, prec, steps):
     peak, kind = measured_peaks()
     ach = BYTES_PER_NODE[prec] * nodes / (ms * 1e-3) / 1e9
     sim.close()
-    return {"precision": prec, "value": nodes / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
-            "variant": variant, "achieved_gbs": ach, "frac": ach / peak,
-            "bytes_per_node": BYTES_PER_NODE[prec]}
+    out = {"precision": prec, "value": nodes / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
+           "variant": variant, "achieved_gbs": ach, "frac": ach / peak,
+           "bytes_per_node": BYTES_PER_NODE[prec]}
+    if prec == "fp64":
+        gops = FP64_OPS_PER_NODE * nodes / (ms * 1e-3) / 1e9
+        out["alu_roofline"] = {"bound": "alu", "achieved": gops, "peak": FP64_PIPE_PEAK_GOPS,
+                               "unit": "G FP64-pipe instructions/s", "frac": gops / FP64_PIPE_PEAK_GOPS,
+                               "note": "403 DADD+DFMA+DMUL per node (ncu); peak 2/SM/cycle x 152 SMs x 2.07 GHz"}
+    return out
 
 
 def single_case(torch, workload, prec, steps):
