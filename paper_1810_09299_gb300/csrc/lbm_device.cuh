@@ -127,18 +127,20 @@ struct CodecF32 {
 
 // 16-bit deviation storage: f_i / (w_i r) - 1/2 (phi-like, centred) and
 // g_i / (w_i r) * scale (rest state g = 0; the scale keeps typical values
-// out of the FP16 subnormal range).
+// out of the FP16 subnormal range).  f is decoded as h wr + wr/2 in one
+// explicit FMA (wr/2 is exact), the same expression for the writer's mass
+// ledger and for the next reader, so both round alike; the g scale is folded
+// into the encoder's reciprocal (a power of two, exact).
 struct CodecH16 {
     using Real = float;
     using PT = __half;
     using F0T = float2;
     static constexpr bool kLedger = true;
     static constexpr float kGScale = 256.0f;
-    // __fmul_rn: never fused into an FMA, so writer (ledger) and reader round alike
-    __device__ static Real dec_f(PT v, Real wr) { return __fmul_rn(__half2float(v) + 0.5f, wr); }
+    __device__ static Real dec_f(PT v, Real wr) { return __fmaf_rn(__half2float(v), wr, 0.5f * wr); }
     __device__ static PT enc_f(Real v, Real, Real inv_wr) { return __float2half_rn(v * inv_wr - 0.5f); }
     __device__ static Real dec_g(PT v, Real wr) { return __half2float(v) * (wr * (1.0f / kGScale)); }
-    __device__ static PT enc_g(Real v, Real, Real inv_wr) { return __float2half_rn(v * inv_wr * kGScale); }
+    __device__ static PT enc_g(Real v, Real, Real inv_wr) { return __float2half_rn(v * (inv_wr * kGScale)); }
 };
 
 struct CodecB16 {
@@ -146,7 +148,7 @@ struct CodecB16 {
     using PT = __nv_bfloat16;
     using F0T = float2;
     static constexpr bool kLedger = true;
-    __device__ static Real dec_f(PT v, Real wr) { return __fmul_rn(__bfloat162float(v) + 0.5f, wr); }
+    __device__ static Real dec_f(PT v, Real wr) { return __fmaf_rn(__bfloat162float(v), wr, 0.5f * wr); }
     __device__ static PT enc_f(Real v, Real, Real inv_wr) { return __float2bfloat16_rn(v * inv_wr - 0.5f); }
     __device__ static Real dec_g(PT v, Real wr) { return __bfloat162float(v) * wr; }
     __device__ static PT enc_g(Real v, Real, Real inv_wr) { return __float2bfloat16_rn(v * inv_wr); }

@@ -94,32 +94,37 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     //    three radii serve every normalisation.
     const Real rinv[3] = {j > 0 ? rcp_(r - (Real)1) : (Real)0, m.inv_r, rcp_(r + (Real)1)};
     const Real rdst[3] = {r - (Real)1, r, r + (Real)1};
-    const bool interior = (j >= 1) && (j + 1 < C.nr) && (k >= 1) && (k + 1 < C.nz);
-    if (interior) {
-        // every link lands on a neighbour inside the domain
-#define AXILBM_PUSH_FAST(I)                                                                                    \
-    fs[I] = store_pair<Codec, I>(V, loc + cz_of(I) * C.pitch + cr_of(I), I, (Real)w_of(I) * rdst[cr_of(I) + 1], \
-                                 (Real)(1.0 / w_of(I)) * rinv[cr_of(I) + 1], fp[I], gp[I]);
-        AXILBM_PUSH_FAST(0)
-        AXILBM_PUSH_FAST(1)
-        AXILBM_PUSH_FAST(2)
-        AXILBM_PUSH_FAST(3)
-        AXILBM_PUSH_FAST(4)
-        AXILBM_PUSH_FAST(5)
-        AXILBM_PUSH_FAST(6)
-        AXILBM_PUSH_FAST(7)
-        AXILBM_PUSH_FAST(8)
+    // A link is special when it leaves the domain: through the axis, the wall
+    // r = nr or a z boundary (wrap or bounce-back).  Every other link lands on
+    // its neighbour and is stored by the branch-free fast path; the node's
+    // special links (at most 5) are then stored by the rules of destination().
+    // A warp that holds one boundary lane thus diverges only over those links.
+    const bool axis = (j == 0), wall = (j + 1 == C.nr), zlo = (k == 0), zhi = (k + 1 == C.nz);
+#define AXILBM_SPECIAL(I) \
+    ((cr_of(I) < 0 && axis) || (cr_of(I) > 0 && wall) || (cz_of(I) < 0 && zlo) || (cz_of(I) > 0 && zhi))
+#define AXILBM_PUSH_FAST(I)                                                                                        \
+    if (!AXILBM_SPECIAL(I))                                                                                        \
+        fs[I] = store_pair<Codec, I>(V, loc + cz_of(I) * C.pitch + cr_of(I), I, (Real)w_of(I) * rdst[cr_of(I) + 1], \
+                                     (Real)(1.0 / w_of(I)) * rinv[cr_of(I) + 1], fp[I], gp[I]);
+    AXILBM_PUSH_FAST(0)
+    AXILBM_PUSH_FAST(1)
+    AXILBM_PUSH_FAST(2)
+    AXILBM_PUSH_FAST(3)
+    AXILBM_PUSH_FAST(4)
+    AXILBM_PUSH_FAST(5)
+    AXILBM_PUSH_FAST(6)
+    AXILBM_PUSH_FAST(7)
+    AXILBM_PUSH_FAST(8)
 #undef AXILBM_PUSH_FAST
-    } else {
-        // boundary nodes: wrap, bounce-back or axis reflection per link
-#define AXILBM_PUSH(I)                                                                                     \
-    {                                                                                                      \
-        const Dest d = destination<I>(k, j, C.nr, C.nz, C.zper);                                           \
-        const int s = d.j - j + 1;                                                                         \
-        fs[I] = store_pair<Codec, I>(V, d.k * C.pitch + d.j, d.dir, (Real)w_of(I) * rdst[s],               \
-                                     (Real)(1.0 / w_of(I)) * rinv[s], fp[I], gp[I]);                       \
+    if (axis || wall || zlo || zhi) {
+        // wrap, bounce-back or axis reflection (the rest direction is never special)
+#define AXILBM_PUSH(I)                                                                         \
+    if (AXILBM_SPECIAL(I)) {                                                                   \
+        const Dest d = destination<I>(k, j, C.nr, C.nz, C.zper);                               \
+        const int s = d.j - j + 1;                                                             \
+        fs[I] = store_pair<Codec, I>(V, d.k * C.pitch + d.j, d.dir, (Real)w_of(I) * rdst[s],   \
+                                     (Real)(1.0 / w_of(I)) * rinv[s], fp[I], gp[I]);           \
     }
-        AXILBM_PUSH(0)
         AXILBM_PUSH(1)
         AXILBM_PUSH(2)
         AXILBM_PUSH(3)
@@ -130,6 +135,7 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
         AXILBM_PUSH(8)
 #undef AXILBM_PUSH
     }
+#undef AXILBM_SPECIAL
     // f_0: the collision's value (FP64), or the mass ledger: incoming total
     // minus the outgoing f_1..8 as they will be read back
     if constexpr (Codec::kLedger) {
