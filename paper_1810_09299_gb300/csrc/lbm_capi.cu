@@ -24,15 +24,22 @@ namespace {
 constexpr int kGraphSteps = 32;  // steps per captured graph (even: parity returns)
 
 size_t pt_size(int prec) { return prec == LBM_FP64 ? 8 : (prec == LBM_FP32 ? 4 : 2); }
-size_t f0_size(int) { return 8; }  // f_0 is FP64 in every precision (mass ledger)
+size_t f0_size(int) { return 8; }  // f_0 is 8 bytes in every precision (FP64, or the FP32 ledger pair)
 size_t real_size(int prec) { return prec == LBM_FP64 ? 8 : 4; }
+// bytes of one storage block (32 nodes) in this precision
+size_t block_bytes(int prec) {
+    return (size_t)block_bytes_of((int)f0_size(prec), (int)pt_size(prec), (int)real_size(prec));
+}
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 int validate(const lbm_params& p) {
     if (p.nr < 2 || p.nz < 2) return LBM_ERR_INVALID_ARG;
-    // 32-bit indexing inside a case: 9 planes of nz * pitch elements must fit
+    // 32-bit indexing inside a case: 9 planes of nz * pitch elements must fit,
+    // and so must the bytes of one row of storage blocks
     if ((int64_t)p.nz * ((p.nr + 31) / 32 * 32) * 9 >= ((int64_t)1 << 31)) return LBM_ERR_INVALID_ARG;
+    if ((int64_t)((p.nr + 31) / 32) * (int64_t)block_bytes(p.precision) >= ((int64_t)1 << 31))
+        return LBM_ERR_INVALID_ARG;
     if (p.z_periodic != 0 && p.z_periodic != 1) return LBM_ERR_INVALID_ARG;
     if (p.precision < LBM_FP64 || p.precision > LBM_MIX_BF16) return LBM_ERR_INVALID_ARG;
     if (p.p_coupling != LBM_P_EXACT && p.p_coupling != LBM_P_LAGGED) return LBM_ERR_INVALID_ARG;
@@ -281,37 +288,27 @@ bool encode_tensor_maps(lbm_sim* h, std::vector<CUtensorMap>& maps) {
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
     const int p = h->precision;
-    const size_t es = pt_size(p), er = real_size(p);
-    auto dtype = [](size_t bytes) {
-        return bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
-                          : (bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64);
-    };
+    const size_t B = block_bytes(p);
     maps.assign((size_t)h->ncases * 2 * kMapsPerCase, CUtensorMap{});
     for (int c = 0; c < h->ncases; ++c) {
         const CaseDev& C = h->cases[c];
+        const int ng = C.pitch / 32;
         for (int set = 0; set < 2; ++set) {
             const cuuint32_t tz = set == 0 ? 8 : 16;
             CUtensorMap* M = &maps[((size_t)c * 2 + set) * kMapsPerCase];
-            auto enc = [&](CUtensorMap* m, void* base, size_t bytes, int rank, cuuint32_t box0, cuuint32_t box1,
-                           cuuint32_t box2, cuuint32_t planes) {
-                const cuuint64_t dims[3] = {(cuuint64_t)C.pitch, (cuuint64_t)C.nz, planes};
-                const cuuint64_t strides[2] = {(cuuint64_t)C.pitch * bytes, (cuuint64_t)C.plane * bytes};
-                const cuuint32_t box[3] = {box0, box1, box2};
-                const cuuint32_t estr[3] = {1, 1, 1};
-                return encode(m, dtype(bytes), rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-            };
+            // the case's blocks as 32-bit words: [rows][column groups][128-byte slots][32 words];
+            // a box is tz + 4 rows of one column group, every slot
             for (int b = 0; b < 2; ++b) {
-                char* fq = (char*)h->D.fq[b] + 8 * C.off * es;
-                char* f0 = (char*)h->D.f0[b] + C.off * 8;
-                char* g = (char*)h->D.g[b] + 9 * C.off * es;
-                if (!enc(M + b, fq, es, 3, kTmaCols, tz + 4, 8, 8)) return false;
-                if (!enc(M + 2 + b, f0, 8, 2, kTmaCols, tz + 4, 1, 1)) return false;
-                if (!enc(M + 4 + b, g, es, 3, 32, tz, 9, 9)) return false;
+                void* base = (char*)h->D.blk[b] + (size_t)(C.off / 32) * B;
+                const cuuint64_t dims[4] = {32, (cuuint64_t)(B / 128), (cuuint64_t)ng, (cuuint64_t)C.nz};
+                const cuuint64_t strides[3] = {128, (cuuint64_t)B, (cuuint64_t)ng * B};
+                const cuuint32_t box[4] = {32, (cuuint32_t)(B / 128), 1, tz + 4};
+                const cuuint32_t estr[4] = {1, 1, 1, 1};
+                if (encode(M + b, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, base, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                    return false;
             }
-            if (!enc(M + 6, (char*)h->D.chi_z + C.off * er, er, 2, 32, tz, 1, 1)) return false;
-            if (!enc(M + 7, (char*)h->D.chi_r + C.off * er, er, 2, 32, tz, 1, 1)) return false;
         }
     }
     return true;
@@ -356,13 +353,8 @@ int create_impl(const lbm_params* cases, int32_t n, void* stream, lbm_handle** o
     };
     const size_t T = (size_t)off;
     for (int b = 0; b < 2; ++b) {
-        A(&h->D.f0[b], T * f0_size(h->precision));
-        A(&h->D.fq[b], 8 * T * pt_size(h->precision));
-        A(&h->D.g[b], 9 * T * pt_size(h->precision));
+        A(&h->D.blk[b], (T / 32) * block_bytes(h->precision));
     }
-    A(&h->D.chi_z, T * real_size(h->precision));
-    A(&h->D.chi_r, T * real_size(h->precision));
-    A(&h->D.p_prev, T * real_size(h->precision));
     A(&h->D.cases, n * sizeof(CaseDev));
     A((void**)&h->fields, 5 * (size_t)h->max_nodes * sizeof(double));
     A((void**)&h->phi0, (size_t)h->max_nodes * sizeof(double));
@@ -648,12 +640,13 @@ int64_t lbm_checkpoint_size(const lbm_handle* h) {
     if (!h) return -1;
     const int64_t T = h->D.total;
     const int p = h->precision;
-    return (int64_t)(T * (f0_size(p) + 17 * pt_size(p) + 3 * real_size(p))) + 8 * (int64_t)h->ncases;
+    return (int64_t)((T / 32) * block_bytes(p)) + 8 * (int64_t)h->ncases;
 }
 
 namespace {
-// Copy the current state (the buffers the next step reads, chi, p^{n-1}) to or
-// from `buf` (host memory, or device memory when `device` is set).
+// Copy the current state (the buffer of storage blocks the next step reads:
+// populations, chi^{n-1}, p^{n-1}) to or from `buf` (host memory, or device
+// memory when `device` is set).
 int checkpoint_copy(lbm_sim* h, void* buf, bool save, bool device = false) {
     const int64_t T = h->D.total;
     const int p = h->precision;
@@ -661,9 +654,7 @@ int checkpoint_copy(lbm_sim* h, void* buf, bool save, bool device = false) {
     struct Part {
         void* dev;
         size_t bytes;
-    } parts[] = {{h->D.f0[a], T * f0_size(p)},     {h->D.fq[a], 8 * T * pt_size(p)},
-                 {h->D.g[a], 9 * T * pt_size(p)},   {h->D.chi_z, T * real_size(p)},
-                 {h->D.chi_r, T * real_size(p)},    {h->D.p_prev, T * real_size(p)}};
+    } parts[] = {{h->D.blk[a], (size_t)(T / 32) * block_bytes(p)}};
     char* cur = (char*)buf;
     for (const Part& q : parts) {
         const cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice

@@ -10,17 +10,18 @@ namespace axilbm {
 struct CaseDev;
 struct TileDev;
 
-// Device buffers of a handle.  Every array is a set of planes of `total`
-// elements; case c occupies elements [off_c, off_c + nz_c * pitch_c) of each
-// plane.  f0 holds f_0 (1 plane), fq holds f_1..f_8 (8 planes), g holds g_0..g_8
-// (9 planes); index [parity] selects the A/B copy read by the next step.
+// Bytes of one storage block (the stored values of 32 nodes: f_0, f_1..8,
+// g_0..8, chi_z, chi_r, p), padded to a multiple of 128 bytes; the element
+// sizes are those of f_0, of a population and of the arithmetic type.
+constexpr int block_bytes_of(int f0_size, int pt_size, int real_size) {
+    return (32 * f0_size + 17 * 32 * pt_size + 3 * 32 * real_size + 127) / 128 * 128;
+}
+
+// Device buffers of a handle: two arrays of `total / 32` blocks (one block per
+// 32 nodes, see Block in lbm_device.cuh); index [parity] selects the buffer
+// read by the next step.
 struct DeviceState {
-    void* f0[2];
-    void* fq[2];
-    void* g[2];
-    void* chi_z;
-    void* chi_r;
-    void* p_prev;
+    void* blk[2];
     void* cases;  // CaseDev[ncases] on the device
     int64_t total;
     bool paper_rates;  // every case uses the rate pattern of the paper's runs (Sec. 3.1)
@@ -51,11 +52,8 @@ constexpr int kNumVariants = 5;
 // variants 3 and 4 stage the tile through shared memory with TMA tensor loads
 constexpr int kVariantTZ[kNumVariants] = {8, 16, 4, 8, 16};
 constexpr bool kVariantTMA[kNumVariants] = {false, false, false, true, true};
-// tensor maps per case and tile height: f_1..8 (parity 0, 1), f_0 (parity 0, 1),
-// g_0..8 (parity 0, 1), chi_z, chi_r
-constexpr int kMapsPerCase = 8;
-constexpr int kTmaHalo = 8;   // columns loaded left of the tile (keeps x 16-byte aligned)
-constexpr int kTmaCols = 48;  // columns per loaded row: 8 + 32 + 8
+// tensor maps per case and tile height: the case's blocks in buffer 0 and 1
+constexpr int kMapsPerCase = 2;
 
 // Diagnostics (lbm_diag.cu): reduce dense FP64 fields of one case into a
 // 11-double record; `partials` is scratch of at least diag_partials_size()

@@ -34,19 +34,19 @@ constexpr int step_min_blocks() {
 }
 
 // Store one post-collision population pair (f_I, g_I) at its destination
-// (local index `dl`, direction `dir`, destination radius normalisation
-// wr / iw).  Returns f_I as the reader will decode it (for the mass ledger).
+// node `dst` as direction `dir`, with the destination radius normalisation
+// wr / iw.  Returns f_I as the reader will decode it (for the mass ledger).
 template <class Codec, int I>
-__device__ __forceinline__ typename Codec::Real store_pair(const CaseView<Codec>& V, int dl, int dir,
-                                                           typename Codec::Real wr, typename Codec::Real iw,
-                                                           typename Codec::Real fpi, typename Codec::Real gpi) {
+__device__ __forceinline__ typename Codec::Real store_pair(const PtRef<Codec>& dst, int dir, typename Codec::Real wr,
+                                                           typename Codec::Real iw, typename Codec::Real fpi,
+                                                           typename Codec::Real gpi) {
     typename Codec::Real stored = fpi;
     if (I != 0) {
         const auto e = Codec::enc_f(fpi, wr, iw);
-        V.fout(dir, dl) = e;
+        dst.f(dir) = e;
         stored = Codec::dec_f(e, wr);
     }
-    V.gout(dir, dl) = Codec::enc_g(gpi, wr, iw);
+    dst.g(dir) = Codec::enc_g(gpi, wr, iw);
     return stored;
 }
 
@@ -81,9 +81,10 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     }
     Real mpf[9], chz, chr;
     collide_f<Real, PR>(C, m, mf, chz_prev, chr_prev, chz, chr, mpf);
-    V.chi_z[loc] = chz;
-    V.chi_r[loc] = chr;
-    if (C.p_coupling == 1) V.p_prev[loc] = m.p;
+    const Node<Codec> own = V.out_node(loc);
+    own.chz() = chz;
+    own.chr() = chr;
+    if (C.p_coupling == 1) own.p() = m.p;
     Real mpg[9];
     collide_g<Real, PR>(C, m, mpg);
     Real fp[9], gp[9];
@@ -100,11 +101,23 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     // special links (at most 5) are then stored by the rules of destination().
     // A warp that holds one boundary lane thus diverges only over those links.
     const bool axis = (j == 0), wall = (j + 1 == C.nr), zlo = (k == 0), zhi = (k + 1 == C.nz);
+    // destination slots of the fast path: the node's own population pointer
+    // plus a row step and a lane step (which crosses into the next or the
+    // previous block at lanes 31 and 0)
+    using PT = typename Codec::PT;
+    constexpr int kB = Block<Codec>::bytes, kPS = (int)sizeof(PT);
+    const int lane = loc & 31;
+    unsigned char* const q0 = V.out_pt(loc).q;
+    const int row = (C.pitch >> 5) * kB;
+    const int step_r = lane == 31 ? kB - 31 * kPS : kPS;
+    const int step_l = lane == 0 ? -(kB - 31 * kPS) : -kPS;
+#define AXILBM_DST(I) \
+    PtRef<Codec>{q0 + (cz_of(I) * row + (cr_of(I) > 0 ? step_r : (cr_of(I) < 0 ? step_l : 0)))}
 #define AXILBM_SPECIAL(I) \
     ((cr_of(I) < 0 && axis) || (cr_of(I) > 0 && wall) || (cz_of(I) < 0 && zlo) || (cz_of(I) > 0 && zhi))
 #define AXILBM_PUSH_FAST(I)                                                                                        \
     if (!AXILBM_SPECIAL(I))                                                                                        \
-        fs[I] = store_pair<Codec, I>(V, loc + cz_of(I) * C.pitch + cr_of(I), I, (Real)w_of(I) * rdst[cr_of(I) + 1], \
+        fs[I] = store_pair<Codec, I>(AXILBM_DST(I), I, (Real)w_of(I) * rdst[cr_of(I) + 1],                        \
                                      (Real)(1.0 / w_of(I)) * rinv[cr_of(I) + 1], fp[I], gp[I]);
     AXILBM_PUSH_FAST(0)
     AXILBM_PUSH_FAST(1)
@@ -122,8 +135,8 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     if (AXILBM_SPECIAL(I)) {                                                                   \
         const Dest d = destination<I>(k, j, C.nr, C.nz, C.zper);                               \
         const int s = d.j - j + 1;                                                             \
-        fs[I] = store_pair<Codec, I>(V, d.k * C.pitch + d.j, d.dir, (Real)w_of(I) * rdst[s],   \
-                                     (Real)(1.0 / w_of(I)) * rinv[s], fp[I], gp[I]);           \
+        fs[I] = store_pair<Codec, I>(V.out_pt(d.k * C.pitch + d.j), d.dir, (Real)w_of(I) * rdst[s], \
+                                     (Real)(1.0 / w_of(I)) * rinv[s], fp[I], gp[I]);                \
     }
         AXILBM_PUSH(1)
         AXILBM_PUSH(2)
@@ -136,15 +149,16 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
 #undef AXILBM_PUSH
     }
 #undef AXILBM_SPECIAL
+#undef AXILBM_DST
     // f_0: the collision's value (FP64), or the mass ledger: incoming total
     // minus the outgoing f_1..8 as they will be read back
     if constexpr (Codec::kLedger) {
 #pragma unroll
         for (int i = 1; i < 5; ++i) ff2_sub(ledger, make_float2((float)fs[i], (float)fs[i + 4]));
         const FF l = ff2_merge(ledger);
-        V.f0_out[loc] = make_float2(l.hi, l.lo);
+        own.f0() = make_float2(l.hi, l.lo);
     } else {
-        V.f0_out[loc] = fp[0];
+        own.f0() = fp[0];
     }
 }
 
@@ -186,14 +200,15 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     PT fraw[8], graw[9];
     Real chz_prev = (Real)0, chr_prev = (Real)0, p_prev = (Real)0;
     if (inside) {
-        f0raw = V.f0_in[loc];
+        const Node<Codec> n = V.in_node(loc);
+        f0raw = n.f0();
 #pragma unroll
-        for (int i = 1; i < 9; ++i) fraw[i - 1] = V.fin(i, loc);
+        for (int i = 1; i < 9; ++i) fraw[i - 1] = n.f(i);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) graw[i] = V.gin(i, loc);
-        chz_prev = V.chi_z[loc];
-        chr_prev = V.chi_r[loc];
-        if (C.p_coupling == 1) p_prev = V.p_prev[loc];
+        for (int i = 0; i < 9; ++i) graw[i] = n.g(i);
+        chz_prev = n.chz();
+        chr_prev = n.chr();
+        if (C.p_coupling == 1) p_prev = n.p();
     }
     // 2. the ring of the phi window (two rows above and below, two columns
     //    left and right of the tile)
@@ -239,43 +254,31 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
 // Shared-memory layout of one stage of the TMA-pipelined step for tile
 // height TZ, then the phi window and one mbarrier per stage.  A stage holds
 // its tile's record, the record of the tile after it in the CTA's walk, the
-// tile's case record and the tile's inputs:
-//   f_1..8, f_0 over rows k0-2 .. k0+TZ+1 and columns j0-8 .. j0+39 (the ring
-//   of the phi window lies inside; x stays 16-byte aligned; cells outside the
-//   arrays read as zero and are never used), g_0..8 and chi over the tile.
+// tile's case record and the storage blocks of the tile's column group for
+// rows k0-2 .. k0+TZ+1 (the tile plus the rows of the phi window's ring; rows
+// outside the case read as zero and are never used).
 template <class Codec, int TZ>
 struct TmaTile {
-    using PT = typename Codec::PT;
-    using F0T = typename Codec::F0T;
     using Real = typename Codec::Real;
     static constexpr int HR = TZ + 4;          // rows k0-2 .. k0+TZ+1
-    static constexpr int HX = kTmaCols;        // columns j0-8 .. j0+39
     static constexpr int LD = kTR + 4;         // phi window row length
     static constexpr size_t al(size_t b) { return (b + 127) / 128 * 128; }
-    static constexpr size_t fq_bytes = (size_t)8 * HR * HX * sizeof(PT);
-    static constexpr size_t f0_bytes = (size_t)HR * HX * sizeof(F0T);
-    static constexpr size_t g_bytes = (size_t)9 * TZ * kTR * sizeof(PT);
-    static constexpr size_t chi_bytes = (size_t)TZ * kTR * sizeof(Real);
+    static constexpr size_t box_bytes = (size_t)HR * Block<Codec>::bytes;
     // offsets inside one stage
     static constexpr size_t off_rec = 0;                   // TileDev of this stage's tile
     static constexpr size_t off_next = 16;                 // TileDev of the CTA's next tile after it
     static constexpr size_t off_case = 32;                 // CaseDev of the tile's case
-    static constexpr size_t off_fq = al(off_case + sizeof(CaseDev));
-    static constexpr size_t off_f0 = al(off_fq + fq_bytes);
-    static constexpr size_t off_g = al(off_f0 + f0_bytes);
-    static constexpr size_t off_chz = al(off_g + g_bytes);
-    static constexpr size_t off_chr = al(off_chz + chi_bytes);
-    static constexpr size_t stage_bytes = al(off_chr + chi_bytes);
+    static constexpr size_t off_box = al(off_case + sizeof(CaseDev));
+    static constexpr size_t stage_bytes = al(off_box + box_bytes);
     // two stages when they fit, else one (FP64 with tall tiles)
     static constexpr int NS = (2 * stage_bytes + 16384 <= 200 * 1024) ? 2 : 1;
     static constexpr size_t off_phi = NS * stage_bytes;
     static constexpr size_t off_bar = al(off_phi + (size_t)HR * LD * sizeof(Real));
     static constexpr size_t bytes = off_bar + 128;
-    static constexpr uint32_t tensor_bytes = (uint32_t)(fq_bytes + f0_bytes + g_bytes + 2 * chi_bytes);
 };
 
 // Fill one stage with tile `tt` (whose successor in the CTA's walk is tile
-// index `next`): records, case record and the five tensor copies, all
+// index `next`): records, case record and one tensor copy of the blocks, all
 // completing on `bar`.  Called by one thread.
 template <class Codec, int BZ>
 __device__ __forceinline__ void tma_issue(unsigned char* stage, const TileDev tt, int next, int ntiles,
@@ -283,26 +286,19 @@ __device__ __forceinline__ void tma_issue(unsigned char* stage, const TileDev tt
                                           int map_set, int parity, uint64_t* bar) {
     using L = TmaTile<Codec, BZ>;
     *(TileDev*)(stage + L::off_rec) = tt;
-    const CUtensorMap* M = maps + ((size_t)tt.c * 2 + map_set) * kMapsPerCase;
-    tensormap_acquire(M + parity);
-    tensormap_acquire(M + 2 + parity);
-    tensormap_acquire(M + 4 + parity);
-    tensormap_acquire(M + 6);
-    tensormap_acquire(M + 7);
+    const CUtensorMap* M = maps + ((size_t)tt.c * 2 + map_set) * kMapsPerCase + parity;
+    tensormap_acquire(M);
     const bool has_next = next < ntiles;
-    mbar_expect_tx(bar, L::tensor_bytes + (uint32_t)sizeof(CaseDev) + (has_next ? (uint32_t)sizeof(TileDev) : 0u));
+    mbar_expect_tx(bar, (uint32_t)L::box_bytes + (uint32_t)sizeof(CaseDev) + (has_next ? (uint32_t)sizeof(TileDev) : 0u));
     bulk_load(stage + L::off_case, cases + tt.c, (uint32_t)sizeof(CaseDev), bar);
     if (has_next) bulk_load(stage + L::off_next, tiles + next, (uint32_t)sizeof(TileDev), bar);
-    tma_load_3d(stage + L::off_fq, M + parity, tt.j0 - kTmaHalo, tt.k0 - 2, 0, bar);
-    tma_load_2d(stage + L::off_f0, M + 2 + parity, tt.j0 - kTmaHalo, tt.k0 - 2, bar);
-    tma_load_3d(stage + L::off_g, M + 4 + parity, tt.j0, tt.k0, 0, bar);
-    tma_load_2d(stage + L::off_chz, M + 6, tt.j0, tt.k0, bar);
-    tma_load_2d(stage + L::off_chr, M + 7, tt.j0, tt.k0, bar);
+    // dims: 32 words, 128-byte slots of a block, column groups, rows
+    tma_load_4d(stage + L::off_box, M, 0, 0, tt.j0 >> 5, tt.k0 - 2, bar);
 }
 
 // phi at window cell (a, b) of tile tt (Eq. 16 + ghost rules), from the
-// staged populations when the ghost-mapped node lies in the staged box, else
-// (a periodic z wrap) from global memory.
+// staged blocks when the ghost-mapped node lies in the tile's column group and
+// the staged rows, else from global memory.
 template <class Codec, int TZ>
 __device__ __forceinline__ typename Codec::Real staged_phi(const unsigned char* st, const CaseDev& C,
                                                            const CaseView<Codec>& V, const TileDev& tt, int a,
@@ -311,14 +307,13 @@ __device__ __forceinline__ typename Codec::Real staged_phi(const unsigned char* 
     using Real = typename Codec::Real;
     const int km = ghost_z(tt.k0 - 2 + a, C.nz, C.zper);
     const int jm = ghost_r(tt.j0 - 2 + b, C.nr);
-    const int sa = km - (tt.k0 - 2), sx = jm - (tt.j0 - kTmaHalo);
+    const int sa = km - (tt.k0 - 2);
     const Real r = (Real)jm + (Real)0.5;
-    if (sa >= 0 && sa < L::HR && sx >= 0 && sx < L::HX) {
-        const typename Codec::PT* s_fq = (const typename Codec::PT*)(st + L::off_fq);
-        const int o = sa * L::HX + sx;
-        Real sum = (Real)f0_value(((const typename Codec::F0T*)(st + L::off_f0))[o]);
+    if (sa >= 0 && sa < L::HR && (jm >> 5) == (tt.j0 >> 5)) {
+        const Node<Codec> n{const_cast<unsigned char*>(st + L::off_box) + (size_t)sa * Block<Codec>::bytes, jm & 31};
+        Real sum = (Real)f0_value(n.f0());
 #pragma unroll
-        for (int i = 1; i < 9; ++i) sum += Codec::dec_f(s_fq[(i - 1) * L::HR * L::HX + o], (Real)w_of(i) * r);
+        for (int i = 1; i < 9; ++i) sum += Codec::dec_f(n.f(i), (Real)w_of(i) * r);
         return sum * rcp_(r);
     }
     return node_phi<Codec>(V, km * C.pitch + jm, r, rcp_(r));
@@ -355,7 +350,7 @@ step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
     using PT = typename Codec::PT;
     using F0T = typename Codec::F0T;
     using L = TmaTile<Codec, BZ>;
-    constexpr int TZ = BZ, HR = L::HR, HX = L::HX, LD = L::LD, NS = L::NS;
+    constexpr int TZ = BZ, LD = L::LD, NS = L::NS;
     constexpr int NRING = 4 * LD + 4 * TZ;
     constexpr int kWaitTries = 1 << 22;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -397,21 +392,22 @@ step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
         const int j = tt.j0 + threadIdx.x;
         const int k = tt.k0 + threadIdx.y;
         const bool inside = (j < C.nr) && (k < C.nz);
-        // own staged inputs
-        const int o = (threadIdx.y + 2) * HX + threadIdx.x + kTmaHalo;
-        const PT* s_fq = (const PT*)(st + L::off_fq);
-        const PT* s_g = (const PT*)(st + L::off_g);
+        // own staged inputs: block of row ty + 2 of the box, lane tx
         F0T f0raw{};
         PT fraw[8], graw[9];
-        Real chz_prev = (Real)0, chr_prev = (Real)0;
+        Real chz_prev = (Real)0, chr_prev = (Real)0, p_prev = (Real)0;
         if (inside) {
-            f0raw = ((const F0T*)(st + L::off_f0))[o];
+            const Node<Codec> n{const_cast<unsigned char*>(st + L::off_box) +
+                                    (size_t)(threadIdx.y + 2) * Block<Codec>::bytes,
+                                (int)threadIdx.x};
+            f0raw = n.f0();
 #pragma unroll
-            for (int i = 1; i < 9; ++i) fraw[i - 1] = s_fq[(i - 1) * HR * HX + o];
+            for (int i = 1; i < 9; ++i) fraw[i - 1] = n.f(i);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) graw[i] = s_g[(i * TZ + threadIdx.y) * kTR + threadIdx.x];
-            chz_prev = ((const Real*)(st + L::off_chz))[threadIdx.y * kTR + threadIdx.x];
-            chr_prev = ((const Real*)(st + L::off_chr))[threadIdx.y * kTR + threadIdx.x];
+            for (int i = 0; i < 9; ++i) graw[i] = n.g(i);
+            chz_prev = n.chz();
+            chr_prev = n.chr();
+            if (C.p_coupling == 1) p_prev = n.p();
         }
         // the ring of the phi window, from the staged box
         for (int q = tid; q < NRING; q += kTR * BZ) {
@@ -445,7 +441,6 @@ step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
         __syncthreads();
         if (inside) {
             const int loc = k * C.pitch + j;
-            const Real p_prev = C.p_coupling == 1 ? V.p_prev[loc] : (Real)0;
             node_update<Codec, PR, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw, graw,
                                        chz_prev, chr_prev, p_prev);
         }
@@ -480,14 +475,15 @@ fields_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ til
     if (j >= C.nr || k >= C.nz) return;
     const int loc = k * C.pitch + j;
     const Real r = (Real)j + (Real)0.5;
+    const Node<Codec> nd = V.in_node(loc);
     Real g[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = Codec::dec_g(V.gin(i, loc), (Real)w_of(i) * r);
+    for (int i = 0; i < 9; ++i) g[i] = Codec::dec_g(nd.g(i), (Real)w_of(i) * r);
     Macro<Real> m;
     Real mg[9];
     moments<Real>(g, mg);
-    node_macros<Real, LD>(C, sphi, threadIdx.y + 2, threadIdx.x + 2, j, mg, g[0],
-                          C.p_coupling == 1 ? V.p_prev[loc] : (Real)0, m);
+    node_macros<Real, LD>(C, sphi, threadIdx.y + 2, threadIdx.x + 2, j, mg, g[0], C.p_coupling == 1 ? nd.p() : (Real)0,
+                          m);
     const int64_t n = (int64_t)C.nz * C.nr, o = (int64_t)k * C.nr + j;
     out[o] = (double)m.phi;
     out[n + o] = (double)m.rho;
@@ -505,10 +501,8 @@ __global__ void init_kernel(CaseDev C, const double* __restrict__ phi0, StateDev
     const int k = blockIdx.y;
     if (j >= C.nr || k >= C.nz) return;
     const CaseView<Codec> V = case_view<Codec>(S, C);
-    auto* f0 = const_cast<typename Codec::F0T*>(V.f0_in);
-    auto* fq = const_cast<typename Codec::PT*>(V.fq_in);
-    auto* gq = const_cast<typename Codec::PT*>(V.g_in);
     const int loc = k * C.pitch + j;
+    const Node<Codec> n = V.in_node(loc);
     const CaseReal<Real>& P = case_params<Real>(C);
     const Real phi = (Real)phi0[(int64_t)k * C.nr + j];
     const Real r = (Real)j + (Real)0.5;
@@ -523,20 +517,20 @@ __global__ void init_kernel(CaseDev C, const double* __restrict__ phi0, StateDev
     for (int i = 1; i < 9; ++i) {
         const Real wr = (Real)w_of(i) * r;
         const auto e = Codec::enc_f(fe[i], wr, (Real)1 / wr);
-        fq[(i - 1) * C.plane + loc] = e;
+        n.f(i) = e;
         if constexpr (Codec::kLedger) ff_add(ledger, -(float)Codec::dec_f(e, wr));
     }
     if constexpr (Codec::kLedger) {
         const FF l = ff_norm(ledger);
-        f0[loc] = make_float2(l.hi, l.lo);
+        n.f0() = make_float2(l.hi, l.lo);
     } else {
-        f0[loc] = fe[0];
+        n.f0() = fe[0];
     }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) gq[i * C.plane + loc] = Codec::enc_g((Real)0, (Real)w_of(i) * r, (Real)1);
-    V.chi_z[loc] = (Real)0;
-    V.chi_r[loc] = P.mob * phi;
-    V.p_prev[loc] = (Real)0;
+    for (int i = 0; i < 9; ++i) n.g(i) = Codec::enc_g((Real)0, (Real)w_of(i) * r, (Real)1);
+    n.chz() = (Real)0;
+    n.chr() = P.mob * phi;
+    n.p() = (Real)0;
 }
 
 // Decode the state of one case into FP64 arrays (f[9], g[9], aux[3], each [nz][nr]).
@@ -547,25 +541,25 @@ __global__ void get_state_kernel(CaseDev C, StateDev<Codec> S, double* f, double
     const int k = blockIdx.y;
     if (j >= C.nr || k >= C.nz) return;
     const CaseView<Codec> V = case_view<Codec>(S, C);
-    const int loc = k * C.pitch + j;
+    const Node<Codec> nd = V.in_node(k * C.pitch + j);
     const int64_t n = (int64_t)C.nz * C.nr, o = (int64_t)k * C.nr + j;
     const Real r = (Real)j + (Real)0.5;
     if (f) {
         if constexpr (Codec::kLedger) {
-            const float2 v = ((const float2*)V.f0_in)[loc];
+            const float2 v = nd.f0();
             f[o] = (double)v.x + (double)v.y;
         } else {
-            f[o] = (double)f0_value(V.f0_in[loc]);
+            f[o] = (double)f0_value(nd.f0());
         }
-        for (int i = 1; i < 9; ++i) f[i * n + o] = (double)Codec::dec_f(V.fin(i, loc), (Real)w_of(i) * r);
+        for (int i = 1; i < 9; ++i) f[i * n + o] = (double)Codec::dec_f(nd.f(i), (Real)w_of(i) * r);
     }
     if (g) {
-        for (int i = 0; i < 9; ++i) g[i * n + o] = (double)Codec::dec_g(V.gin(i, loc), (Real)w_of(i) * r);
+        for (int i = 0; i < 9; ++i) g[i * n + o] = (double)Codec::dec_g(nd.g(i), (Real)w_of(i) * r);
     }
     if (aux) {
-        aux[o] = (double)V.chi_z[loc];
-        aux[n + o] = (double)V.chi_r[loc];
-        aux[2 * n + o] = (double)V.p_prev[loc];
+        aux[o] = (double)nd.chz();
+        aux[n + o] = (double)nd.chr();
+        aux[2 * n + o] = (double)nd.p();
     }
 }
 
@@ -577,10 +571,7 @@ __global__ void set_state_kernel(CaseDev C, StateDev<Codec> S, const double* f, 
     const int k = blockIdx.y;
     if (j >= C.nr || k >= C.nz) return;
     const CaseView<Codec> V = case_view<Codec>(S, C);
-    auto* f0 = const_cast<typename Codec::F0T*>(V.f0_in);
-    auto* fq = const_cast<typename Codec::PT*>(V.fq_in);
-    auto* gq = const_cast<typename Codec::PT*>(V.g_in);
-    const int loc = k * C.pitch + j;
+    const Node<Codec> nd = V.in_node(k * C.pitch + j);
     const int64_t n = (int64_t)C.nz * C.nr, o = (int64_t)k * C.nr + j;
     const Real r = (Real)j + (Real)0.5;
     if (f) {
@@ -592,51 +583,45 @@ __global__ void set_state_kernel(CaseDev C, StateDev<Codec> S, const double* f, 
             for (int i = 1; i < 9; ++i) {
                 const Real wr = (Real)w_of(i) * r;
                 const auto e = Codec::enc_f((Real)f[i * n + o], wr, (Real)1 / wr);
-                fq[(i - 1) * C.plane + loc] = e;
+                nd.f(i) = e;
                 ff_add(ledger, (float)f[i * n + o]);
                 ff_add(ledger, (float)(f[i * n + o] - (double)(float)f[i * n + o]));
                 ff_add(ledger, -(float)Codec::dec_f(e, wr));
             }
             const FF l = ff_norm(ledger);
-            ((float2*)f0)[loc] = make_float2(l.hi, l.lo);
+            *reinterpret_cast<float2*>(&nd.f0()) = make_float2(l.hi, l.lo);
         } else {
             for (int i = 1; i < 9; ++i) {
                 const Real wr = (Real)w_of(i) * r;
-                fq[(i - 1) * C.plane + loc] = Codec::enc_f((Real)f[i * n + o], wr, (Real)1 / wr);
+                nd.f(i) = Codec::enc_f((Real)f[i * n + o], wr, (Real)1 / wr);
             }
-            ((double*)f0)[loc] = f[o];
+            *reinterpret_cast<double*>(&nd.f0()) = f[o];
         }
     }
     if (g) {
         for (int i = 0; i < 9; ++i) {
             const Real wr = (Real)w_of(i) * r;
-            gq[i * C.plane + loc] = Codec::enc_g((Real)g[i * n + o], wr, (Real)1 / wr);
+            nd.g(i) = Codec::enc_g((Real)g[i * n + o], wr, (Real)1 / wr);
         }
     }
     if (aux) {
-        V.chi_z[loc] = (Real)aux[o];
-        V.chi_r[loc] = (Real)aux[n + o];
-        V.p_prev[loc] = (Real)aux[2 * n + o];
+        nd.chz() = (Real)aux[o];
+        nd.chr() = (Real)aux[n + o];
+        nd.p() = (Real)aux[2 * n + o];
     }
 }
 
 // ---------------------------------------------------------------- host launchers
 template <class Codec>
 StateDev<Codec> make_state(const DeviceState& D, int parity) {
-    using PT = typename Codec::PT;
-    using F0T = typename Codec::F0T;
-    using Real = typename Codec::Real;
+    static_assert(Block<Codec>::bytes == block_bytes_of((int)sizeof(typename Codec::F0T),
+                                                        (int)sizeof(typename Codec::PT),
+                                                        (int)sizeof(typename Codec::Real)),
+                  "host and device block sizes");
     StateDev<Codec> S;
     const int a = parity & 1, b = a ^ 1;
-    S.f0_in = (const F0T*)D.f0[a];
-    S.fq_in = (const PT*)D.fq[a];
-    S.g_in = (const PT*)D.g[a];
-    S.f0_out = (F0T*)D.f0[b];
-    S.fq_out = (PT*)D.fq[b];
-    S.g_out = (PT*)D.g[b];
-    S.chi_z = (Real*)D.chi_z;
-    S.chi_r = (Real*)D.chi_r;
-    S.p_prev = (Real*)D.p_prev;
+    S.in = (const unsigned char*)D.blk[a];
+    S.out = (unsigned char*)D.blk[b];
     return S;
 }
 
