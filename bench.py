@@ -45,9 +45,10 @@ BYTES_PER_NODE = {
 DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf16": "f32 (bf16 storage)"}
 # DRAM bytes per node update of the step kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the nodes of the captured
-# launch; profiles/step_kernel_fp32_batched64cases.md).  Scaled to a full
-# launch by the node count.  Kept only for the kernel build that was captured.
-TRAFFIC_B_PER_NODE = {}
+# launch; profiles/step_kernel_fp32_batched64cases.md), keyed by precision and
+# launch variant.  Scaled to a full launch by the node count.  Kept only for
+# the kernel build that was captured.
+TRAFFIC_B_PER_NODE = {("fp32", 0): 159.75}
 # The FP64 step is bound by the FP64 pipe, not by HBM: FP64-pipe thread
 # instructions (DADD + DFMA + DMUL) per node update from one ncu capture
 # (profiles/step_kernel_fp64_batched64cases.md), against the pipe's peak of
@@ -302,7 +303,8 @@ def run_cuda(args):
                    "variant": variant, "parallelism": f"independent cases per GPU x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": (TRAFFIC_B_PER_NODE[prec] * nodes if prec in TRAFFIC_B_PER_NODE else None),
+                     "traffic": (TRAFFIC_B_PER_NODE[(prec, variant)] * nodes
+                                 if (prec, variant) in TRAFFIC_B_PER_NODE else None),
                      "traffic_unit": "bytes per launch (ncu capture of 64 cases scaled by node count)",
                      "note": f"peak {peak_kind}; algorithmic bytes {BYTES_PER_NODE[prec]} B/node x {nodes} nodes "
                              f"per launch / mean CUDA-event launch duration"},

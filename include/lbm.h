@@ -186,6 +186,8 @@ int lbm_checkpoint_load(lbm_handle* h, const void* host_buf);
 
 /* Time a few launch shapes of the step kernel on the current state (which is
  * saved and restored, so the simulation does not advance) and keep the fastest.
+ * Candidates are timed in index order; a later one must be at least 1 % faster
+ * than the best so far to replace it, so near ties keep the earlier shape.
  * reps >= 1 timed steps per candidate.  Writes the chosen variant index to
  * *chosen (may be NULL).  Synchronises. */
 int lbm_autotune(lbm_handle* h, int32_t reps, int32_t* chosen);

@@ -734,7 +734,9 @@ int lbm_autotune(lbm_handle* h, int32_t reps, int32_t* chosen) {
         if (rc == LBM_OK) rc = cuda_ok(h, cudaEventSynchronize(e1));
         float ms = 0.f;
         if (rc == LBM_OK) cudaEventElapsedTime(&ms, e0, e1);
-        if (rc == LBM_OK && ms < best) {
+        // a later candidate must be at least 1 % faster to replace an earlier
+        // one, so near ties keep the earlier (default) launch shape
+        if (rc == LBM_OK && ms < 0.99f * best) {
             best = ms;
             best_v = v;
         }
