@@ -11,6 +11,10 @@
 namespace axilbm {
 
 constexpr int kTR = 32;  // tile width along r = one warp
+// L2 prefetch distance of the step in quarters of a resident wave of CTAs
+// (SMs x CTAs per SM).  Measured on the 512-case batch: anything from 3/4 to
+// 3/2 of a wave gives the same time, half a wave or two waves less.
+constexpr int kPrefetchQuarters = 4;
 
 // phi at window position (a, b) of tile t through the ghost rules.
 template <class Codec>
@@ -169,7 +173,8 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
 // recomputed from neighbours' populations.
 template <class Codec, int BZ, bool PR>
 __global__ void __launch_bounds__(kTR * BZ, (step_min_blocks<Codec, BZ, PR>()))
-step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles, StateDev<Codec> S) {
+step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles, StateDev<Codec> S,
+            const CUtensorMap* __restrict__ maps, int map_set, int parity, int ntiles, int ahead) {
     using Real = typename Codec::Real;
     using PT = typename Codec::PT;
     using F0T = typename Codec::F0T;
@@ -182,6 +187,15 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     __shared__ __align__(16) CaseDev sC;
     static_assert(sizeof(CaseDev) % 4 == 0 && sizeof(CaseDev) / 4 <= kTR * BZ, "one word per thread");
     const TileDev t = tiles[blockIdx.x];
+    // L2 prefetch of the blocks of the tile one resident wave ahead (a CTA
+    // that will start about when this one ends): one tensor prefetch, issued
+    // by one thread; the tensor maps are absent when they could not be made
+    if (maps != nullptr && threadIdx.x == 0 && threadIdx.y == 0 && (int)blockIdx.x + ahead < ntiles) {
+        const TileDev tp = tiles[blockIdx.x + ahead];
+        const CUtensorMap* M = maps + ((size_t)tp.c * 2 + map_set) * kMapsPerCase + parity;
+        tensormap_acquire(M);
+        tma_prefetch_4d(M, 0, 0, tp.j0 >> 5, tp.k0 - 2);
+    }
     {
         const int q = threadIdx.y * kTR + threadIdx.x;
         if (q < (int)(sizeof(CaseDev) / 4))
@@ -648,10 +662,28 @@ void launch_tma(int ntiles, cudaStream_t st, const CaseDev* cs, const TileDev* t
 template <class Codec, bool PR>
 void launch_step_rates(int variant, int ntiles, cudaStream_t st, const CaseDev* cs, const TileDev* tiles,
                        const StateDev<Codec>& S, const DeviceState& D, int parity) {
+    // prefetch distance: the CTAs resident at once (SMs x CTAs per SM)
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    const CUtensorMap* maps = (const CUtensorMap*)D.tmaps;
     switch (variant) {
-        case 0: step_kernel<Codec, 8, PR><<<ntiles, dim3(kTR, 8), 0, st>>>(cs, tiles, S); break;
-        case 1: step_kernel<Codec, 16, PR><<<ntiles, dim3(kTR, 16), 0, st>>>(cs, tiles, S); break;
-        case 2: step_kernel<Codec, 4, PR><<<ntiles, dim3(kTR, 4), 0, st>>>(cs, tiles, S); break;
+        case 0:
+            step_kernel<Codec, 8, PR><<<ntiles, dim3(kTR, 8), 0, st>>>(
+                cs, tiles, S, maps, 0, parity, ntiles, kPrefetchQuarters * sms * step_min_blocks<Codec, 8, PR>() / 4);
+            break;
+        case 1:
+            step_kernel<Codec, 16, PR><<<ntiles, dim3(kTR, 16), 0, st>>>(
+                cs, tiles, S, maps, 1, parity, ntiles, kPrefetchQuarters * sms * step_min_blocks<Codec, 16, PR>() / 4);
+            break;
+        case 2:
+            step_kernel<Codec, 4, PR><<<ntiles, dim3(kTR, 4), 0, st>>>(
+                cs, tiles, S, maps, 0, parity, ntiles, kPrefetchQuarters * sms * step_min_blocks<Codec, 4, PR>() / 4);
+            break;
         case 3: launch_tma<Codec, 8, PR>(ntiles, st, cs, tiles, S, D, parity); break;
         default: launch_tma<Codec, 16, PR>(ntiles, st, cs, tiles, S, D, parity); break;
     }
