@@ -125,8 +125,9 @@ typedef enum {
 enum { LBM_FIELD_PHI = 1, LBM_FIELD_RHO = 2, LBM_FIELD_UZ = 4, LBM_FIELD_UR = 8, LBM_FIELD_P = 16 };
 
 /* Create a single-case handle.  stream: a cudaStream_t (NULL = default stream).
- * Validates the parameters (LBM_ERR_INVALID_ARG), allocates the device state
- * (LBM_ERR_OOM) and selects the current CUDA device.  *out is set on success. */
+ * Validates the parameters (LBM_ERR_INVALID_ARG; among them nz * pitch < 2^31
+ * with pitch = nr rounded up to 32), allocates the device state (LBM_ERR_OOM)
+ * and selects the current CUDA device.  *out is set on success. */
 int lbm_create(const lbm_params* prm, void* stream, lbm_handle** out);
 
 /* Create a batch of ncases independent cases (ncases >= 1) that advance together:

@@ -35,9 +35,9 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 int validate(const lbm_params& p) {
     if (p.nr < 2 || p.nz < 2) return LBM_ERR_INVALID_ARG;
-    // 32-bit indexing inside a case: 9 planes of nz * pitch elements must fit,
-    // and so must the bytes of one row of storage blocks
-    if ((int64_t)p.nz * ((p.nr + 31) / 32 * 32) * 9 >= ((int64_t)1 << 31)) return LBM_ERR_INVALID_ARG;
+    // 32-bit node indices inside a case (nz * pitch), and 32-bit byte offsets
+    // across one row of storage blocks
+    if ((int64_t)p.nz * ((p.nr + 31) / 32 * 32) >= ((int64_t)1 << 31)) return LBM_ERR_INVALID_ARG;
     if ((int64_t)((p.nr + 31) / 32) * (int64_t)block_bytes(p.precision) >= ((int64_t)1 << 31))
         return LBM_ERR_INVALID_ARG;
     if (p.z_periodic != 0 && p.z_periodic != 1) return LBM_ERR_INVALID_ARG;
