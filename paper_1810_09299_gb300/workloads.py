@@ -130,6 +130,19 @@ def oscillating_drop(nr=128, nz=256, R0=32.0, eps=0.05, zc=None, ratio=100.0, **
     return c
 
 
+def paper_ellipsoid(Rr=30.0, ratio=100.0, Rz=90.0, **kw):
+    """The paper's oscillating ellipsoid (Sec. 3.2, Tables 1 and 2): a 300 x 150
+    (z x r) domain, periodic in z, drop centred at (150, 0) with half-axes
+    R_z = 90 and R_r, in the paper's density scale rho_g = 1, rho_l = ratio;
+    W = 4, sigma = 0.3, M = 0.01, nu_l = nu_g = 0.1, the paper's rates."""
+    c = base_case(nr=150, nz=300, z_periodic=1, rho_l=float(ratio), rho_g=1.0, nu_l=0.1, nu_g=0.1,
+                  sigma=0.3, W=4.0, mobility=0.01)
+    c.update(shape="ellipsoid", shape_args=[150.0, float(Rz), float(Rr), 4.0], steps=60000)
+    c.update(kw)
+    c["shape_args"][-1] = c["W"]
+    return c
+
+
 def thread_breakup(nr=64, R0=20.0, k_wave=0.7, amp_frac=0.1, seed=None, **kw):
     """Liquid thread on the axis, periodic z of one wavelength lambda = 2 pi R0 / k
     (nz = ceil(lambda)), radius perturbation amp_frac * R0 with a seeded phase."""
