@@ -297,14 +297,15 @@ bool encode_tensor_maps(lbm_sim* h, std::vector<CUtensorMap>& maps) {
             const cuuint32_t tz = set == 0 ? 8 : 16;
             CUtensorMap* M = &maps[((size_t)c * 2 + set) * kMapsPerCase];
             // the case's blocks as 32-bit words: [rows][column groups][128-byte slots][32 words];
-            // a box is tz + 4 rows of one column group, every slot
-            for (int b = 0; b < 2; ++b) {
+            // a box is tz + 4 rows (staging) or tz rows (prefetch) of one column group, every slot
+            for (int m = 0; m < 4; ++m) {
+                const int b = m & 1;
                 void* base = (char*)h->D.blk[b] + (size_t)(C.off / 32) * B;
                 const cuuint64_t dims[4] = {32, (cuuint64_t)(B / 128), (cuuint64_t)ng, (cuuint64_t)C.nz};
                 const cuuint64_t strides[3] = {128, (cuuint64_t)B, (cuuint64_t)ng * B};
-                const cuuint32_t box[4] = {32, (cuuint32_t)(B / 128), 1, tz + 4};
+                const cuuint32_t box[4] = {32, (cuuint32_t)(B / 128), 1, m < 2 ? tz + 4 : tz};
                 const cuuint32_t estr[4] = {1, 1, 1, 1};
-                if (encode(M + b, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, base, dims, strides, box, estr,
+                if (encode(M + m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, base, dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
                     return false;

@@ -53,7 +53,9 @@ constexpr int kNumVariants = 5;
 constexpr int kVariantTZ[kNumVariants] = {8, 16, 4, 8, 16};
 constexpr bool kVariantTMA[kNumVariants] = {false, false, false, true, true};
 // tensor maps per case and tile height: the case's blocks in buffer 0 and 1
-constexpr int kMapsPerCase = 2;
+// with a box of the tile's rows plus two above and below (staging, [0], [1]),
+// and with a box of the tile's rows only (L2 prefetch, [2], [3])
+constexpr int kMapsPerCase = 4;
 
 // Diagnostics (lbm_diag.cu): reduce dense FP64 fields of one case into a
 // 11-double record; `partials` is scratch of at least diag_partials_size()

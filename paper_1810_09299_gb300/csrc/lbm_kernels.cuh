@@ -192,9 +192,9 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     // by one thread; the tensor maps are absent when they could not be made
     if (maps != nullptr && threadIdx.x == 0 && threadIdx.y == 0 && (int)blockIdx.x + ahead < ntiles) {
         const TileDev tp = tiles[blockIdx.x + ahead];
-        const CUtensorMap* M = maps + ((size_t)tp.c * 2 + map_set) * kMapsPerCase + parity;
+        const CUtensorMap* M = maps + ((size_t)tp.c * 2 + map_set) * kMapsPerCase + 2 + parity;
         tensormap_acquire(M);
-        tma_prefetch_4d(M, 0, 0, tp.j0 >> 5, tp.k0 - 2);
+        tma_prefetch_4d(M, 0, 0, tp.j0 >> 5, tp.k0);
     }
     {
         const int q = threadIdx.y * kTR + threadIdx.x;
