@@ -109,6 +109,7 @@ struct CodecF64 {
     using PT = double;
     using F0T = double;
     static constexpr bool kLedger = false;
+    static constexpr bool kStreamStores = false;
     __device__ static Real dec_f(PT v, Real) { return v; }
     __device__ static PT enc_f(Real v, Real, Real) { return v; }
     __device__ static Real dec_g(PT v, Real) { return v; }
@@ -120,12 +121,16 @@ struct CodecF32 {
     using PT = float;
     using F0T = float2;
     static constexpr bool kLedger = true;
+    static constexpr bool kStreamStores = false;
     __device__ static Real dec_f(PT v, Real) { return v; }
     __device__ static PT enc_f(Real v, Real, Real) { return v; }
     __device__ static Real dec_g(PT v, Real) { return v; }
     __device__ static PT enc_g(Real v, Real, Real) { return v; }
 };
 
+// kStreamStores: the step writes its pushed populations with evict-first
+// stores (measured: -1.5 % on the 16-bit step, +2.8 % on the FP32 one).
+//
 // 16-bit deviation storage: f_i / (w_i r) - 1/2 (phi-like, centred) and
 // g_i / (w_i r) * scale (rest state g = 0; the scale keeps typical values
 // out of the FP16 subnormal range).  f is decoded as h wr + wr/2 in one
@@ -137,6 +142,7 @@ struct CodecH16 {
     using PT = __half;
     using F0T = float2;
     static constexpr bool kLedger = true;
+    static constexpr bool kStreamStores = true;
     static constexpr float kGScale = 256.0f;
     __device__ static Real dec_f(PT v, Real wr) { return __fmaf_rn(__half2float(v), wr, 0.5f * wr); }
     __device__ static PT enc_f(Real v, Real, Real inv_wr) { return __float2half_rn(v * inv_wr - 0.5f); }
@@ -149,6 +155,7 @@ struct CodecB16 {
     using PT = __nv_bfloat16;
     using F0T = float2;
     static constexpr bool kLedger = true;
+    static constexpr bool kStreamStores = true;
     __device__ static Real dec_f(PT v, Real wr) { return __fmaf_rn(__bfloat162float(v), wr, 0.5f * wr); }
     __device__ static PT enc_f(Real v, Real, Real inv_wr) { return __float2bfloat16_rn(v * inv_wr - 0.5f); }
     __device__ static Real dec_g(PT v, Real wr) { return __bfloat162float(v) * wr; }

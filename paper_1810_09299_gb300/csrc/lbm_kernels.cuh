@@ -47,10 +47,12 @@ __device__ __forceinline__ typename Codec::Real store_pair(const PtRef<Codec>& d
     typename Codec::Real stored = fpi;
     if (I != 0) {
         const auto e = Codec::enc_f(fpi, wr, iw);
-        dst.f(dir) = e;
+        if constexpr (Codec::kStreamStores) __stcs(&dst.f(dir), e);
+        else dst.f(dir) = e;
         stored = Codec::dec_f(e, wr);
     }
-    dst.g(dir) = Codec::enc_g(gpi, wr, iw);
+    if constexpr (Codec::kStreamStores) __stcs(&dst.g(dir), Codec::enc_g(gpi, wr, iw));
+    else dst.g(dir) = Codec::enc_g(gpi, wr, iw);
     return stored;
 }
 
