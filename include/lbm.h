@@ -149,6 +149,14 @@ int lbm_init_phase(lbm_handle* h, int32_t shape, const double* shape_args, int32
 int lbm_case_init_phase(lbm_handle* h, int32_t icase, int32_t shape, const double* shape_args,
                         int32_t nargs, const double* host_phi);
 
+/* The same initial condition for every case of the handle at once, from host
+ * arrays: host_phi holds each case's phi0 ([nz][nr] doubles) one after the
+ * other, in case order (sum over cases of nz * nr doubles).  One host-to-device
+ * copy and one synchronisation for the whole batch, instead of one per case.
+ * The first call allocates a device staging array of that size, kept until
+ * lbm_destroy.  Resets every step counter.  Synchronises. */
+int lbm_init_phase_all(lbm_handle* h, const double* host_phi);
+
 /* Advance every case by nsteps time steps (nsteps >= 0).  One step is
  * Eq. 16 (phi) -> Eq. 39-40 (stencils) -> Eq. 4, 17, 35 -> Eq. 32-33 (u, p) ->
  * Eq. 30 (force) -> Eq. 19-23 (phase-field collision) -> Eq. 24-29, 36-37
@@ -169,6 +177,29 @@ int lbm_case_get_fields(lbm_handle* h, int32_t icase, int32_t mask, double* host
  * LBM_ERR_NONFINITE (and fills *out) if any phi, u or p is not finite. */
 int lbm_diagnostics(lbm_handle* h, lbm_diag* out);
 int lbm_case_diagnostics(lbm_handle* h, int32_t icase, lbm_diag* out);
+
+/* Pipelined diagnostics: the record of lbm_case_diagnostics (the quantities
+ * Sec. 3.1-3.3 read off the runs), enqueued on the handle's stream without
+ * waiting, so that a loop reading one record per step keeps the GPU busy:
+ * enqueue step n and its record, enqueue step n+1, then wait for record n.
+ *   host_out  the lbm_diag the record is copied into when the stream gets
+ *             there.  Unlike other host pointers it is kept beyond the call:
+ *             it must stay valid until lbm_diagnostics_wait on its slot
+ *             returns.  Use page-locked (pinned) memory; with pageable memory
+ *             the copy, and with it this call, completes before returning.
+ *   slot      0 .. LBM_DIAG_SLOTS - 1, names the record for the wait; an
+ *             enqueue on a slot replaces the slot's previous record (wait for
+ *             that one first).
+ * Returns LBM_ERR_INVALID_ARG for a bad case or slot or a NULL host_out,
+ * LBM_ERR_STATE if the case has no initial condition.  Does not synchronise. */
+#define LBM_DIAG_SLOTS 4
+int lbm_case_diagnostics_enqueue(lbm_handle* h, int32_t icase, lbm_diag* host_out, int32_t slot);
+
+/* Wait until the record enqueued on `slot` is in its host_out.  Returns
+ * LBM_ERR_TIMEOUT if a bounded device wait gave up before it, LBM_ERR_NONFINITE
+ * if the record counts non-finite values (both sticky, as for
+ * lbm_case_diagnostics), LBM_ERR_STATE if nothing is pending on the slot. */
+int lbm_diagnostics_wait(lbm_handle* h, int32_t slot);
 
 /* Populations of case icase as FP64 host arrays f[9][nz][nr], g[9][nz][nr] and the
  * time-level state aux[3][nz][nr] = (chi_z^{n-1}, chi_r^{n-1}, p^{n-1}); any pointer

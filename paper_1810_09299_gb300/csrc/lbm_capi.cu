@@ -92,12 +92,26 @@ struct lbm_sim {
     int64_t max_nodes = 0;  // largest nz * nr of a case
     double* fields = nullptr;   // [5][nz][nr] of the largest case
     double* phi0 = nullptr;     // [nz][nr]
+    double* phi0_all = nullptr;  // every case's [nz][nr], made by the first lbm_init_phase_all
     double* state = nullptr;    // [21][nz][nr]
     double* partials = nullptr;
     double* diag_out = nullptr;
     // pinned host staging for small reads (a diagnostics record and the
     // status word), so that they return with one synchronisation
     double* host_small = nullptr;
+    // pipelined diagnostics: per slot a completion event, the caller's record
+    // and a pinned copy of the device status word
+    cudaEvent_t diag_ev[LBM_DIAG_SLOTS] = {};
+    lbm_diag* slot_out[LBM_DIAG_SLOTS] = {};
+    int* slot_status = nullptr;
+    // Pipelined diagnostics run on a private stream beside the next steps:
+    // ev_state marks the state they read, ev_fields the end of that read (the
+    // handle's stream waits for it before it overwrites the state), ev_diag
+    // the end of their use of the shared scratch (fields, partials, record),
+    // which the handle's stream joins before it uses that scratch itself.
+    cudaStream_t diag_stream = nullptr;
+    cudaEvent_t ev_state = nullptr, ev_fields = nullptr, ev_diag = nullptr;
+    bool diag_pending = false;
     std::vector<void*> allocations;
     int parity = 0;
     int variant = 0;
@@ -144,24 +158,24 @@ cudaError_t launch_step_any(lbm_sim* h, int parity, int variant, cudaStream_t st
     }
 }
 
-cudaError_t launch_fields_any(lbm_sim* h, int icase) {
+cudaError_t launch_fields_any(lbm_sim* h, int icase, cudaStream_t st) {
     const TileDev* t = h->ftiles_d[icase];
     const int n = h->nftiles[icase];
     switch (h->precision) {
-        case LBM_FP64: return launch_fields_f64(h->D, h->parity, t, n, h->fields, h->stream);
-        case LBM_FP32: return launch_fields_f32(h->D, h->parity, t, n, h->fields, h->stream);
-        case LBM_MIX_FP16: return launch_fields_h16(h->D, h->parity, t, n, h->fields, h->stream);
-        default: return launch_fields_b16(h->D, h->parity, t, n, h->fields, h->stream);
+        case LBM_FP64: return launch_fields_f64(h->D, h->parity, t, n, h->fields, st);
+        case LBM_FP32: return launch_fields_f32(h->D, h->parity, t, n, h->fields, st);
+        case LBM_MIX_FP16: return launch_fields_h16(h->D, h->parity, t, n, h->fields, st);
+        default: return launch_fields_b16(h->D, h->parity, t, n, h->fields, st);
     }
 }
 
-cudaError_t launch_init_any(lbm_sim* h, int icase) {
+cudaError_t launch_init_any(lbm_sim* h, int icase, const double* phi0) {
     const CaseDev& C = h->cases[icase];
     switch (h->precision) {
-        case LBM_FP64: return launch_init_f64(h->D, h->parity, C, h->phi0, h->stream);
-        case LBM_FP32: return launch_init_f32(h->D, h->parity, C, h->phi0, h->stream);
-        case LBM_MIX_FP16: return launch_init_h16(h->D, h->parity, C, h->phi0, h->stream);
-        default: return launch_init_b16(h->D, h->parity, C, h->phi0, h->stream);
+        case LBM_FP64: return launch_init_f64(h->D, h->parity, C, phi0, h->stream);
+        case LBM_FP32: return launch_init_f32(h->D, h->parity, C, phi0, h->stream);
+        case LBM_MIX_FP16: return launch_init_h16(h->D, h->parity, C, phi0, h->stream);
+        default: return launch_init_b16(h->D, h->parity, C, phi0, h->stream);
     }
 }
 
@@ -259,21 +273,37 @@ int upload_tiles(lbm_sim* h, const std::vector<TileDev>& t, TileDev** out) {
 }
 
 void release(lbm_sim* h) {
-    if (h->host_small) cudaFreeHost(h->host_small);
-    h->host_small = nullptr;
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
     for (void* p : h->allocations) cudaFreeAsync(p, h->stream);
     h->allocations.clear();
+    // every copy still pending into the pinned buffers below ends here
     cudaStreamSynchronize(h->stream);
+    if (h->diag_stream) cudaStreamSynchronize(h->diag_stream);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->cap_stream = nullptr;
+    if (h->diag_stream) cudaStreamDestroy(h->diag_stream);
+    h->diag_stream = nullptr;
+    for (cudaEvent_t* e : {&h->ev_state, &h->ev_fields, &h->ev_diag}) {
+        if (*e) cudaEventDestroy(*e);
+        *e = nullptr;
+    }
+    if (h->host_small) cudaFreeHost(h->host_small);
+    h->host_small = nullptr;
+    if (h->slot_status) cudaFreeHost(h->slot_status);
+    h->slot_status = nullptr;
+    for (cudaEvent_t& e : h->diag_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
 }
 
-// Tensor maps of the TMA-staged step (see step_kernel_tma): per case and per
-// tile height (8, 16 rows): f_1..8 (3-D, parity 0/1), f_0 (2-D, parity 0/1),
-// g_0..8 (3-D, parity 0/1), chi_z, chi_r (2-D).  Returns false when the driver
-// entry point is missing or a map is rejected; the TMA variants are then unused.
+// Tensor maps of the step's storage blocks (kMapsPerCase per case and per tile
+// height of 8 and 16 rows): the TMA-pipelined step stages boxes of the tile's
+// rows plus two above and below, and the register-path step prefetches boxes
+// of the tile's own rows into L2.  Returns false when the driver entry point
+// is missing or a map is rejected; the TMA variants and the prefetch are then
+// unused.
 bool encode_tensor_maps(lbm_sim* h, std::vector<CUtensorMap>& maps) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -367,6 +397,23 @@ int create_impl(const lbm_params* cases, int32_t n, void* stream, lbm_handle** o
         cudaGetLastError();
         h->host_small = nullptr;
         rc = LBM_ERR_OOM;
+    }
+    if (rc == LBM_OK && cudaMallocHost((void**)&h->slot_status, LBM_DIAG_SLOTS * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        h->slot_status = nullptr;
+        rc = LBM_ERR_OOM;
+    }
+    for (int q = 0; q < LBM_DIAG_SLOTS && rc == LBM_OK; ++q)
+        if (cudaEventCreateWithFlags(&h->diag_ev[q], cudaEventDisableTiming) != cudaSuccess) rc = LBM_ERR_CUDA;
+    for (cudaEvent_t* e : {&h->ev_state, &h->ev_fields, &h->ev_diag})
+        if (rc == LBM_OK && cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) rc = LBM_ERR_CUDA;
+    // the diagnostics stream has the greatest priority, so that its few blocks
+    // are scheduled ahead of the next step's tiles instead of after them
+    if (rc == LBM_OK) {
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&h->diag_stream, cudaStreamNonBlocking, greatest) != cudaSuccess)
+            rc = LBM_ERR_CUDA;
     }
     if (rc == LBM_OK) {
         std::vector<CUtensorMap> maps;
@@ -470,6 +517,50 @@ int check_case(lbm_sim* h, int icase) {
     return LBM_OK;
 }
 
+// Order the handle's stream after the pipelined diagnostics' use of the
+// shared scratch (fields, partials, record) before it uses that scratch.
+int join_diagnostics(lbm_sim* h) {
+    if (!h->diag_pending) return LBM_OK;
+    int rc = cuda_ok(h, cudaStreamWaitEvent(h->stream, h->ev_diag, 0));
+    if (rc == LBM_OK) h->diag_pending = false;
+    return rc;
+}
+
+// Enqueue the fields and the reductions of case icase, then the copies of the
+// 11-double record to `record` and of the device status word to `status`
+// (host memory), on stream `st`.  When st is the diagnostics stream, the
+// fields' read of the state is ordered after the work already on the handle's
+// stream, and the handle's stream waits for that read only.  Does not wait.
+int enqueue_diagnostics(lbm_sim* h, int icase, double* record, int* status, cudaStream_t st) {
+    const bool side = st != h->stream;
+    int rc = LBM_OK;
+    if (side) {
+        rc = cuda_ok(h, cudaEventRecord(h->ev_state, h->stream));
+        if (rc == LBM_OK) rc = cuda_ok(h, cudaStreamWaitEvent(st, h->ev_state, 0));
+    } else {
+        rc = join_diagnostics(h);
+    }
+    if (rc != LBM_OK) return rc;
+    rc = cuda_ok(h, launch_fields_any(h, icase, st));
+    if (rc != LBM_OK) return rc;
+    if (side) {
+        rc = cuda_ok(h, cudaEventRecord(h->ev_fields, st));
+        if (rc == LBM_OK) rc = cuda_ok(h, cudaStreamWaitEvent(h->stream, h->ev_fields, 0));
+        if (rc != LBM_OK) return rc;
+    }
+    const lbm_params& p = h->prm[icase];
+    rc = cuda_ok(h, launch_diag(h->fields, p.nz, p.nr, p.z_periodic, (double)h->case_steps[icase], h->partials,
+                                h->diag_out, st));
+    if (rc != LBM_OK) return rc;
+    rc = cuda_ok(h, cudaMemcpyAsync(record, h->diag_out, 11 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (rc != LBM_OK) return rc;
+    rc = cuda_ok(h, cudaMemcpyAsync(status, h->D.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (rc != LBM_OK || !side) return rc;
+    rc = cuda_ok(h, cudaEventRecord(h->ev_diag, st));
+    if (rc == LBM_OK) h->diag_pending = true;
+    return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -501,10 +592,37 @@ int lbm_case_init_phase(lbm_handle* h, int32_t icase, int32_t shape, const doubl
         rc = cuda_ok(h, launch_shape(shape, shape_args, nargs, p.nz, p.nr, h->phi0, h->stream));
     }
     if (rc != LBM_OK) return rc;
-    rc = cuda_ok(h, launch_init_any(h, icase));
+    rc = cuda_ok(h, launch_init_any(h, icase, h->phi0));
     if (rc != LBM_OK) return rc;
     h->case_steps[icase] = 0;
     h->initialized[icase] = 1;
+    return cuda_ok(h, cudaStreamSynchronize(h->stream));
+}
+
+int lbm_init_phase_all(lbm_handle* h, const double* host_phi) {
+    int rc = enter(h);
+    if (rc != LBM_OK) return rc;
+    if (!host_phi) return LBM_ERR_INVALID_ARG;
+    int64_t total = 0;
+    for (const lbm_params& p : h->prm) total += (int64_t)p.nz * p.nr;
+    if (!h->phi0_all) {
+        void* p = nullptr;
+        rc = cuda_ok(h, dev_alloc(h, &p, (size_t)total * sizeof(double)));
+        if (rc != LBM_OK) return rc;
+        h->phi0_all = (double*)p;
+    }
+    rc = cuda_ok(h, cudaMemcpyAsync(h->phi0_all, host_phi, (size_t)total * sizeof(double), cudaMemcpyHostToDevice,
+                                    h->stream));
+    int64_t o = 0;
+    for (int c = 0; c < h->ncases && rc == LBM_OK; ++c) {
+        rc = cuda_ok(h, launch_init_any(h, c, h->phi0_all + o));
+        o += (int64_t)h->prm[c].nz * h->prm[c].nr;
+    }
+    if (rc != LBM_OK) return rc;
+    for (int c = 0; c < h->ncases; ++c) {
+        h->case_steps[c] = 0;
+        h->initialized[c] = 1;
+    }
     return cuda_ok(h, cudaStreamSynchronize(h->stream));
 }
 
@@ -550,7 +668,9 @@ int lbm_case_get_fields(lbm_handle* h, int32_t icase, int32_t mask, double* host
     if (!h->initialized[icase]) return LBM_ERR_STATE;
     rc = check_status(h);
     if (rc != LBM_OK) return rc;
-    rc = cuda_ok(h, launch_fields_any(h, icase));
+    rc = join_diagnostics(h);
+    if (rc != LBM_OK) return rc;
+    rc = cuda_ok(h, launch_fields_any(h, icase, h->stream));
     if (rc != LBM_OK) return rc;
     const int64_t n = (int64_t)h->prm[icase].nz * h->prm[icase].nr;
     int slot = 0;
@@ -572,17 +692,9 @@ int lbm_case_diagnostics(lbm_handle* h, int32_t icase, lbm_diag* out) {
     if (check_case(h, icase) != LBM_OK || !out) return LBM_ERR_INVALID_ARG;
     if (!h->initialized[icase]) return LBM_ERR_STATE;
     // the record and the device status word come back with one synchronisation
-    rc = cuda_ok(h, launch_fields_any(h, icase));
-    if (rc != LBM_OK) return rc;
-    const lbm_params& p = h->prm[icase];
-    rc = cuda_ok(h, launch_diag(h->fields, p.nz, p.nr, p.z_periodic, (double)h->case_steps[icase], h->partials,
-                                h->diag_out, h->stream));
-    if (rc != LBM_OK) return rc;
     double* buf = h->host_small;          // 11 doubles of the record
     int* st_h = (int*)(h->host_small + 12);  // the status word
-    rc = cuda_ok(h, cudaMemcpyAsync(buf, h->diag_out, 11 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    if (rc != LBM_OK) return rc;
-    rc = cuda_ok(h, cudaMemcpyAsync(st_h, h->D.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    rc = enqueue_diagnostics(h, icase, buf, st_h, h->stream);
     if (rc != LBM_OK) return rc;
     rc = cuda_ok(h, cudaStreamSynchronize(h->stream));
     if (rc != LBM_OK) return rc;
@@ -597,6 +709,36 @@ int lbm_case_diagnostics(lbm_handle* h, int32_t icase, lbm_diag* out) {
 }
 
 int lbm_diagnostics(lbm_handle* h, lbm_diag* out) { return lbm_case_diagnostics(h, 0, out); }
+
+int lbm_case_diagnostics_enqueue(lbm_handle* h, int32_t icase, lbm_diag* host_out, int32_t slot) {
+    int rc = enter(h);
+    if (rc != LBM_OK) return rc;
+    if (check_case(h, icase) != LBM_OK || !host_out || slot < 0 || slot >= LBM_DIAG_SLOTS) return LBM_ERR_INVALID_ARG;
+    if (!h->initialized[icase]) return LBM_ERR_STATE;
+    rc = enqueue_diagnostics(h, icase, (double*)host_out, h->slot_status + slot, h->diag_stream);
+    if (rc != LBM_OK) return rc;
+    rc = cuda_ok(h, cudaEventRecord(h->diag_ev[slot], h->diag_stream));
+    if (rc != LBM_OK) return rc;
+    h->slot_out[slot] = host_out;
+    return LBM_OK;
+}
+
+int lbm_diagnostics_wait(lbm_handle* h, int32_t slot) {
+    int rc = enter(h);
+    if (rc != LBM_OK) return rc;
+    if (slot < 0 || slot >= LBM_DIAG_SLOTS) return LBM_ERR_INVALID_ARG;
+    lbm_diag* out = h->slot_out[slot];
+    if (!out) return LBM_ERR_STATE;
+    rc = cuda_ok(h, cudaEventSynchronize(h->diag_ev[slot]));
+    if (rc != LBM_OK) return rc;
+    h->slot_out[slot] = nullptr;
+    if (h->slot_status[slot] != 0) {
+        h->sticky = LBM_ERR_TIMEOUT;
+        return LBM_ERR_TIMEOUT;
+    }
+    if (out->nonfinite > 0) return fail(h, LBM_ERR_NONFINITE);
+    return LBM_OK;
+}
 
 int lbm_get_state(lbm_handle* h, int32_t icase, double* f, double* g, double* aux) {
     int rc = enter(h);

@@ -36,8 +36,9 @@ EXPORTS = (
     "lbm_get_state", "lbm_set_state", "lbm_checkpoint_size", "lbm_checkpoint_save",
     "lbm_checkpoint_load", "lbm_autotune", "lbm_set_variant", "lbm_num_variants",
     "lbm_kernel_launches", "lbm_destroy", "lbm_strerror", "lbm_diag_reduce_noalloc",
-    "lbm_selftest_bounded_wait",
+    "lbm_selftest_bounded_wait", "lbm_case_diagnostics_enqueue", "lbm_diagnostics_wait", "lbm_init_phase_all",
 )
+DIAG_SLOTS = 4
 
 
 class LbmParams(ctypes.Structure):
@@ -103,6 +104,9 @@ def lib():
         "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "lbm_diag_reduce_noalloc": (ctypes.c_int, [vp, i32, i32, i32, ctypes.c_double, vp, vp]),
         "lbm_selftest_bounded_wait": (ctypes.c_int, [i32, vp, vp]),
+        "lbm_case_diagnostics_enqueue": (ctypes.c_int, [vp, i32, ctypes.POINTER(LbmDiag), i32]),
+        "lbm_diagnostics_wait": (ctypes.c_int, [vp, i32]),
+        "lbm_init_phase_all": (ctypes.c_int, [vp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -212,6 +216,14 @@ class Simulation:
         _check(rc, "lbm_init_phase")
         return self
 
+    def init_all(self, phi_all: np.ndarray):
+        """Every case from host arrays at once: phi_all holds each case's
+        [nz][nr] phi0 one after the other (C-contiguous float64)."""
+        need = sum(c["nz"] * c["nr"] for c in self.cases)
+        assert phi_all.dtype == np.float64 and phi_all.flags["C_CONTIGUOUS"] and phi_all.size == need
+        _check(lib().lbm_init_phase_all(self._h, _dp(phi_all)), "lbm_init_phase_all")
+        return self
+
     def init_case(self, icase: int, case: Optional[dict] = None, host_array: bool = True):
         """Initial phi of a workloads.py case dict: from its host array or its shape."""
         from . import workloads
@@ -244,6 +256,15 @@ class Simulation:
         out = {k: getattr(d, k) for k, _ in LbmDiag._fields_}
         out["status"] = rc
         return out
+
+    def diagnostics_enqueue(self, icase: int, out: "LbmDiag", slot: int):
+        """Enqueue case icase's record into `out` (keep it alive, and pinned for
+        the copy to be asynchronous, until diagnostics_wait(slot))."""
+        _check(lib().lbm_case_diagnostics_enqueue(self._h, icase, ctypes.byref(out), slot), "lbm_diagnostics_enqueue")
+
+    def diagnostics_wait(self, slot: int) -> int:
+        """Wait for the record enqueued on `slot`; returns the status code."""
+        return int(lib().lbm_diagnostics_wait(self._h, slot))
 
     def state(self, icase: int = 0):
         c = self.cases[icase]
