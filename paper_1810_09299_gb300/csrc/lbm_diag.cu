@@ -33,81 +33,130 @@ struct KSum {
 };
 
 // Quantities: 0 mass, 1 kinetic, 2 z-moment, 3 p in liquid, 4 weight in liquid,
-// 5 p in gas, 6 weight in gas (sums); 7 umax, 8 phi_min, 9 phi_max (extrema);
-// 10 non-finite count (sum).
-__global__ void __launch_bounds__(kDiagThreads) diag_partial_kernel(const double* __restrict__ F, int nz, int nr,
-                                                                    double* __restrict__ partials) {
-    const int64_t n = (int64_t)nz * nr;
-    KSum acc[7] = {};
-    double umax = 0.0, pmin = INFINITY, pmax = -INFINITY, bad = 0.0;
-    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(o / nr), j = (int)(o - (int64_t)k * nr);
-        const double r = j + 0.5, z = k + 0.5;
-        const double phi = F[o], rho = F[n + o], uz = F[2 * n + o], ur = F[3 * n + o], p = F[4 * n + o];
-        if (!isfinite(phi) || !isfinite(uz) || !isfinite(ur) || !isfinite(p)) {
-            bad += 1.0;
-            continue;
-        }
-        const double uu = uz * uz + ur * ur;
-        acc[0].add(r * phi);
-        acc[1].add(0.5 * r * rho * uu);
-        acc[2].add(r * z * phi);
-        if (phi > 0.99) {
-            acc[3].add(r * p);
-            acc[4].add(r);
-        }
-        if (phi < 0.01) {
-            acc[5].add(r * p);
-            acc[6].add(r);
-        }
-        umax = fmax(umax, sqrt(uu));
-        pmin = fmin(pmin, phi);
-        pmax = fmax(pmax, phi);
-    }
-    __shared__ double sh[kDiagThreads][2 * 7 + 4];
-    for (int q = 0; q < 7; ++q) {
-        sh[threadIdx.x][2 * q] = acc[q].s;
-        sh[threadIdx.x][2 * q + 1] = acc[q].c;
-    }
-    sh[threadIdx.x][14] = umax;
-    sh[threadIdx.x][15] = pmin;
-    sh[threadIdx.x][16] = pmax;
-    sh[threadIdx.x][17] = bad;
-    __syncthreads();
-    for (int stride = kDiagThreads / 2; stride > 0; stride >>= 1) {
-        if (threadIdx.x < stride) {
-            double* a = sh[threadIdx.x];
-            const double* b = sh[threadIdx.x + stride];
-            for (int q = 0; q < 7; ++q) {
-                KSum x{a[2 * q], a[2 * q + 1]};
-                x.merge(KSum{b[2 * q], b[2 * q + 1]});
-                a[2 * q] = x.s;
-                a[2 * q + 1] = x.c;
-            }
-            a[14] = fmax(a[14], b[14]);
-            a[15] = fmin(a[15], b[15]);
-            a[16] = fmax(a[16], b[16]);
-            a[17] += b[17];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < 18; ++q) partials[blockIdx.x * 18 + q] = sh[0][q];
-    }
+// 5 p in gas, 6 weight in gas (sums); 7 max |u|^2, 8 phi_min, 9 phi_max
+// (extrema); 10 non-finite count (sum).  A partial record is 18 doubles:
+// (sum, compensation) of quantities 0-6, then 7-10.
+constexpr int kSums = 7;
+
+// A compensated pair (s, c) from lane + off of the warp (a shuffle of both).
+__device__ __forceinline__ KSum shfl_down_ksum(const KSum& x, int off) {
+    return KSum{__shfl_down_sync(0xffffffffu, x.s, off), __shfl_down_sync(0xffffffffu, x.c, off)};
 }
 
-// One partial record: 7 compensated sums, 3 extrema, the non-finite count.
-__device__ __forceinline__ void merge_partial(double* a, const double* b) {
-    for (int q = 0; q < 7; ++q) {
-        KSum x{a[2 * q], a[2 * q + 1]};
-        x.merge(KSum{b[2 * q], b[2 * q + 1]});
-        a[2 * q] = x.s;
-        a[2 * q + 1] = x.c;
+// Combine the compensated pairs (v, vc)[0 .. count) held in shared memory with
+// stride `stride` (one per partial record) into lane 0 of the calling warp:
+// each lane merges its share in a fixed order, then a fixed shuffle tree
+// merges the lanes.  Every sum is compensated (Neumaier).
+__device__ __forceinline__ KSum warp_ksum(const double* v, const double* vc, int count, int stride) {
+    const int lane = threadIdx.x & 31;
+    KSum acc{0.0, 0.0};
+    for (int i = lane; i < count; i += 32) acc.merge(KSum{v[(size_t)i * stride], vc[(size_t)i * stride]});
+    for (int off = 16; off > 0; off >>= 1) {
+        const KSum o = shfl_down_ksum(acc, off);
+        if (lane + off < 32) acc.merge(o);
     }
-    a[14] = fmax(a[14], b[14]);
-    a[15] = fmin(a[15], b[15]);
-    a[16] = fmax(a[16], b[16]);
-    a[17] += b[17];
+    return acc;
+}
+
+// The plain sum of v[0 .. count) (stride as above) into lane 0: each lane adds
+// its share in a fixed order, then a fixed pairwise shuffle tree.  Used inside
+// a block, where a thread holds few nodes: pairwise summation of the block's
+// values keeps the error near log2(values) rounding units.
+__device__ __forceinline__ double warp_sum(const double* v, int count, int stride) {
+    const int lane = threadIdx.x & 31;
+    double acc = 0.0;
+    for (int i = lane; i < count; i += 32) acc += v[(size_t)i * stride];
+    for (int off = 16; off > 0; off >>= 1) {
+        const double o = __shfl_down_sync(0xffffffffu, acc, off);
+        if (lane + off < 32) acc += o;
+    }
+    return acc;
+}
+
+// The extrema and the count the same way: max |u|^2, min phi, max phi, count.
+__device__ __forceinline__ void warp_extrema(const double* uu, const double* lo, const double* hi,
+                                             const double* bad, int count, int stride, double out[4]) {
+    const int lane = threadIdx.x & 31;
+    double m = 0.0, mn = INFINITY, mx = -INFINITY, nb = 0.0;
+    for (int i = lane; i < count; i += 32) {
+        m = fmax(m, uu[(size_t)i * stride]);
+        mn = fmin(mn, lo[(size_t)i * stride]);
+        mx = fmax(mx, hi[(size_t)i * stride]);
+        nb += bad[(size_t)i * stride];
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+        mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, off));
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+        const double o = __shfl_down_sync(0xffffffffu, nb, off);
+        if (lane + off < 32) nb += o;
+    }
+    out[0] = m;
+    out[1] = mn;
+    out[2] = mx;
+    out[3] = nb;
+}
+
+// One partial record per block.  Rows k = blockIdx.x, blockIdx.x + gridDim.x,
+// ...; within a row each thread takes the columns j = threadIdx.x + 256 i, so a
+// thread holds only a few nodes and sums them plainly; the block's 256 values
+// of each quantity are then summed pairwise by one warp per quantity (warps
+// 0-6 the sums, warp 7 the extrema and the count).  The records of the blocks
+// are combined with compensated sums by diag_final_kernel.
+__global__ void __launch_bounds__(kDiagThreads) diag_partial_kernel(const double* __restrict__ F, int nz, int nr,
+                                                                    double* __restrict__ partials) {
+    static_assert(kDiagThreads == 32 * (kSums + 1), "one warp per sum plus one");
+    const int64_t n = (int64_t)nz * nr;
+    double acc[kSums] = {};
+    double uu_max = 0.0, pmin = INFINITY, pmax = -INFINITY, bad = 0.0;
+    for (int k = blockIdx.x; k < nz; k += gridDim.x) {
+        const double z = k + 0.5;
+        for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+            const int64_t o = (int64_t)k * nr + j;
+            const double r = j + 0.5;
+            const double phi = F[o], rho = F[n + o], uz = F[2 * n + o], ur = F[3 * n + o], p = F[4 * n + o];
+            if (!isfinite(phi) || !isfinite(uz) || !isfinite(ur) || !isfinite(p)) {
+                bad += 1.0;
+                continue;
+            }
+            const double uu = uz * uz + ur * ur;
+            acc[0] += r * phi;
+            acc[1] += 0.5 * r * rho * uu;
+            acc[2] += r * z * phi;
+            if (phi > 0.99) {
+                acc[3] += r * p;
+                acc[4] += r;
+            }
+            if (phi < 0.01) {
+                acc[5] += r * p;
+                acc[6] += r;
+            }
+            uu_max = fmax(uu_max, uu);
+            pmin = fmin(pmin, phi);
+            pmax = fmax(pmax, phi);
+        }
+    }
+    __shared__ double sh[kSums + 4][kDiagThreads];
+    for (int q = 0; q < kSums; ++q) sh[q][threadIdx.x] = acc[q];
+    sh[kSums][threadIdx.x] = uu_max;
+    sh[kSums + 1][threadIdx.x] = pmin;
+    sh[kSums + 2][threadIdx.x] = pmax;
+    sh[kSums + 3][threadIdx.x] = bad;
+    __syncthreads();
+    const int w = threadIdx.x >> 5;
+    double* out = partials + (size_t)blockIdx.x * 18;
+    if (w < kSums) {
+        const double t = warp_sum(sh[w], kDiagThreads, 1);
+        if ((threadIdx.x & 31) == 0) {
+            out[2 * w] = t;
+            out[2 * w + 1] = 0.0;
+        }
+    } else {
+        double e[4];
+        warp_extrema(sh[kSums], sh[kSums + 1], sh[kSums + 2], sh[kSums + 3], kDiagThreads, 1, e);
+        if ((threadIdx.x & 31) == 0)
+            for (int q = 0; q < 4; ++q) out[14 + q] = e[q];
+    }
 }
 
 // Contribution of the axis link (k, k+1) to the length of the phi > 1/2 set on
@@ -127,28 +176,36 @@ __device__ __forceinline__ double axis_link(const double* __restrict__ F, int k,
     return 0.0;
 }
 
-// Final combination and the interface lengths, one block of kFinalThreads.
-// Every sum runs in a fixed order (fixed-shape trees), so the result is
-// deterministic.
+// Final combination and the interface lengths, one block of kFinalThreads:
+// warps 0-6 combine one sum each over the partial records and warp 7 the
+// extrema and the count, every one in a fixed order (compensated sums), so
+// the result is deterministic.
 constexpr int kFinalThreads = 256;
-static_assert(kDiagBlocks <= 2 * kFinalThreads, "one fold into the first kFinalThreads partials");
+static_assert(kFinalThreads == 32 * (kSums + 1), "one warp per sum plus one");
 __global__ void __launch_bounds__(kFinalThreads) diag_final_kernel(const double* __restrict__ F, int nz, int nr,
                                                                    int zper, double step,
                                                                    const double* __restrict__ partials,
                                                                    double* __restrict__ out) {
     __shared__ double sp[kDiagBlocks][18];
+    __shared__ double sres[18];
     __shared__ double slen[kFinalThreads];
     __shared__ int sjmin;
     const int t = threadIdx.x;
     for (int i = t; i < kDiagBlocks * 18; i += kFinalThreads) (&sp[0][0])[i] = partials[i];
     if (t == 0) sjmin = nr;
     __syncthreads();
-    // partial records: fold kDiagBlocks into kFinalThreads, then a halving tree
-    if (t + kFinalThreads < kDiagBlocks) merge_partial(sp[t], sp[t + kFinalThreads]);
-    __syncthreads();
-    for (int stride = kFinalThreads / 2; stride > 0; stride >>= 1) {
-        if (t < stride) merge_partial(sp[t], sp[t + stride]);
-        __syncthreads();
+    const int w = t >> 5;
+    if (w < kSums) {
+        const KSum r = warp_ksum(&sp[0][2 * w], &sp[0][2 * w + 1], kDiagBlocks, 18);
+        if ((t & 31) == 0) {
+            sres[2 * w] = r.s;
+            sres[2 * w + 1] = r.c;
+        }
+    } else {
+        double e[4];
+        warp_extrema(&sp[0][14], &sp[0][15], &sp[0][16], &sp[0][17], kDiagBlocks, 18, e);
+        if ((t & 31) == 0)
+            for (int q = 0; q < 4; ++q) sres[14 + q] = e[q];
     }
     // axis half-length: per-thread sums over k = t, t + T, ... then a halving tree
     double len = 0.0;
@@ -159,8 +216,9 @@ __global__ void __launch_bounds__(kFinalThreads) diag_final_kernel(const double*
         if (t < stride) slen[t] += slen[t + stride];
         __syncthreads();
     }
-    const double mass = KSum{sp[0][0], sp[0][1]}.value();
-    const double zc = KSum{sp[0][4], sp[0][5]}.value() / mass;
+    __syncthreads();
+    const double mass = KSum{sres[0], sres[1]}.value();
+    const double zc = KSum{sres[4], sres[5]}.value() / mass;
     // radial crossing on the row nearest the centroid: the first outward crossing
     int kc = (int)floor(zc);
     kc = kc < 0 ? 0 : (kc >= nz ? nz - 1 : kc);
@@ -180,20 +238,20 @@ __global__ void __launch_bounds__(kFinalThreads) diag_final_kernel(const double*
     }
     double axis = slen[0];
     if (!zper && F[0] - 0.5 > 0) axis += 0.5;
-    const double win = KSum{sp[0][8], sp[0][9]}.value(), wout = KSum{sp[0][12], sp[0][13]}.value();
-    const double dp = (win > 0 ? KSum{sp[0][6], sp[0][7]}.value() / win : 0.0) -
-                      (wout > 0 ? KSum{sp[0][10], sp[0][11]}.value() / wout : 0.0);
+    const double win = KSum{sres[8], sres[9]}.value(), wout = KSum{sres[12], sres[13]}.value();
+    const double dp = (win > 0 ? KSum{sres[6], sres[7]}.value() / win : 0.0) -
+                      (wout > 0 ? KSum{sres[10], sres[11]}.value() / wout : 0.0);
     out[0] = step;
     out[1] = mass;
-    out[2] = KSum{sp[0][2], sp[0][3]}.value();
+    out[2] = KSum{sres[2], sres[3]}.value();
     out[3] = zc;
     out[4] = dp;
-    out[5] = sp[0][14];
-    out[6] = sp[0][15];
-    out[7] = sp[0][16];
+    out[5] = sqrt(sres[14]);  // |u|max from the largest |u|^2
+    out[6] = sres[15];
+    out[7] = sres[16];
     out[8] = 0.5 * axis;
     out[9] = rc;
-    out[10] = sp[0][17];
+    out[10] = sres[17];
 }
 
 // ---------------------------------------------------------------- shapes
