@@ -110,22 +110,26 @@ struct CodecF64 {
     using F0T = double;
     static constexpr bool kLedger = false;
     static constexpr bool kStreamStores = false;
+    using PT2 = double2;  // (f_i, g_i) of one direction, stored together
     __device__ static Real dec_f(PT v, Real) { return v; }
     __device__ static PT enc_f(Real v, Real, Real) { return v; }
     __device__ static Real dec_g(PT v, Real) { return v; }
     __device__ static PT enc_g(Real v, Real, Real) { return v; }
+    __device__ static PT2 enc_pair(Real f, Real g, Real, Real) { return make_double2(f, g); }
 };
 
 struct CodecF32 {
     using Real = float;
     using PT = float;
     using F0T = float2;
+    using PT2 = float2;
     static constexpr bool kLedger = true;
     static constexpr bool kStreamStores = false;
     __device__ static Real dec_f(PT v, Real) { return v; }
     __device__ static PT enc_f(Real v, Real, Real) { return v; }
     __device__ static Real dec_g(PT v, Real) { return v; }
     __device__ static PT enc_g(Real v, Real, Real) { return v; }
+    __device__ static PT2 enc_pair(Real f, Real g, Real, Real) { return make_float2(f, g); }
 };
 
 // kStreamStores: the step writes its pushed populations with evict-first
@@ -141,6 +145,7 @@ struct CodecH16 {
     using Real = float;
     using PT = __half;
     using F0T = float2;
+    using PT2 = __half2;
     static constexpr bool kLedger = true;
     static constexpr bool kStreamStores = true;
     static constexpr float kGScale = 256.0f;
@@ -148,18 +153,26 @@ struct CodecH16 {
     __device__ static PT enc_f(Real v, Real, Real inv_wr) { return __float2half_rn(v * inv_wr - 0.5f); }
     __device__ static Real dec_g(PT v, Real wr) { return __half2float(v) * (wr * (1.0f / kGScale)); }
     __device__ static PT enc_g(Real v, Real, Real inv_wr) { return __float2half_rn(v * (inv_wr * kGScale)); }
+    // both values of a direction in one packed conversion
+    __device__ static PT2 enc_pair(Real f, Real g, Real, Real inv_wr) {
+        return __floats2half2_rn(f * inv_wr - 0.5f, g * (inv_wr * kGScale));
+    }
 };
 
 struct CodecB16 {
     using Real = float;
     using PT = __nv_bfloat16;
     using F0T = float2;
+    using PT2 = __nv_bfloat162;
     static constexpr bool kLedger = true;
     static constexpr bool kStreamStores = true;
     __device__ static Real dec_f(PT v, Real wr) { return __fmaf_rn(__bfloat162float(v), wr, 0.5f * wr); }
     __device__ static PT enc_f(Real v, Real, Real inv_wr) { return __float2bfloat16_rn(v * inv_wr - 0.5f); }
     __device__ static Real dec_g(PT v, Real wr) { return __bfloat162float(v) * wr; }
     __device__ static PT enc_g(Real v, Real, Real inv_wr) { return __float2bfloat16_rn(v * inv_wr); }
+    __device__ static PT2 enc_pair(Real f, Real g, Real, Real inv_wr) {
+        return __floats2bfloat162_rn(f * inv_wr - 0.5f, g * inv_wr);
+    }
 };
 
 // f_0 as a value of the arithmetic type.
@@ -170,58 +183,70 @@ __device__ __forceinline__ float f0_value(float2 v) { return v.x + v.y; }
 // Nodes are stored in groups of 32 consecutive nodes of one row: node L of
 // the handle lies in group L / 32 at lane L % 32.  Each group owns one block
 // per state buffer holding every stored value of its 32 nodes,
-//   f_0 [32 x F0T] | f_1..8 [8][32 x PT] | g_0..8 [9][32 x PT] | chi_z, chi_r, p [3][32 x Real],
-// padded to a multiple of 128 bytes.  A warp reads or writes one value of its
-// 32 nodes as one contiguous run, and all runs of a node group lie together
-// in memory, so the step's 21 streams per node share DRAM pages and
-// translation entries (a pure data-movement test of the step's traffic moved
-// 13 % more bytes per second this way than with one plane per array).
-// chi and p live in both buffers: the step reads them from the buffer it
-// reads and writes them to the buffer it writes.
+//   f_0 [32 x F0T] | (f_i, g_i) for i = 1..8 [8][32 x 2 PT] | g_0 [32 x PT] |
+//   (chi_z, chi_r) [32 x 2 Real] | p [32 x Real],
+// padded to a multiple of 128 bytes.  f_i and g_i of a direction are always
+// pushed to the same neighbour, so they are stored side by side and move as
+// one vector access.  A warp reads or writes one slot of its 32 nodes as one
+// contiguous run, and all runs of a node group lie together in memory, so the
+// step's streams per node share DRAM pages and translation entries (a pure
+// data-movement test of the step's traffic moved 13 % more bytes per second
+// this way than with one plane per array).  chi and p live in both buffers:
+// the step reads them from the buffer it reads and writes them to the buffer
+// it writes.
 template <class Codec>
 struct Block {
     using PT = typename Codec::PT;
     using F0T = typename Codec::F0T;
     using Real = typename Codec::Real;
     static constexpr int off_f0 = 0;
-    static constexpr int off_fq = 32 * (int)sizeof(F0T);
-    static constexpr int off_g = off_fq + 8 * 32 * (int)sizeof(PT);
-    static constexpr int off_chz = off_g + 9 * 32 * (int)sizeof(PT);
-    static constexpr int off_chr = off_chz + 32 * (int)sizeof(Real);
-    static constexpr int off_p = off_chr + 32 * (int)sizeof(Real);
+    static constexpr int off_pairs = 32 * (int)sizeof(F0T);
+    static constexpr int pair_slot = 32 * 2 * (int)sizeof(PT);  // bytes of one direction's pair slot
+    static constexpr int off_g0 = off_pairs + 8 * pair_slot;
+    static constexpr int off_chi = off_g0 + 32 * (int)sizeof(PT);
+    static constexpr int off_p = off_chi + 32 * 2 * (int)sizeof(Real);
     static constexpr int bytes = block_bytes_of((int)sizeof(F0T), (int)sizeof(PT), (int)sizeof(Real));
     static_assert(off_p + 32 * (int)sizeof(Real) <= bytes, "block layout");
+    static_assert(sizeof(typename Codec::PT2) == 2 * sizeof(PT), "pair type");
 };
 
 // One node's values in one buffer: its group's block and its lane.
 template <class Codec>
 struct Node {
     using PT = typename Codec::PT;
+    using PT2 = typename Codec::PT2;
     using F0T = typename Codec::F0T;
     using Real = typename Codec::Real;
     using L = Block<Codec>;
     unsigned char* blk;
     int lane;
     __device__ __forceinline__ F0T& f0() const { return reinterpret_cast<F0T*>(blk + L::off_f0)[lane]; }
-    __device__ __forceinline__ PT& f(int i) const { return reinterpret_cast<PT*>(blk + L::off_fq)[(i - 1) * 32 + lane]; }
-    __device__ __forceinline__ PT& g(int i) const { return reinterpret_cast<PT*>(blk + L::off_g)[i * 32 + lane]; }
-    __device__ __forceinline__ Real& chz() const { return reinterpret_cast<Real*>(blk + L::off_chz)[lane]; }
-    __device__ __forceinline__ Real& chr() const { return reinterpret_cast<Real*>(blk + L::off_chr)[lane]; }
+    // the (f_i, g_i) pair of direction i = 1..8
+    __device__ __forceinline__ PT2& pair(int i) const {
+        return reinterpret_cast<PT2*>(blk + L::off_pairs + (i - 1) * L::pair_slot)[lane];
+    }
+    __device__ __forceinline__ PT& f(int i) const {
+        return reinterpret_cast<PT*>(blk + L::off_pairs + (i - 1) * L::pair_slot)[2 * lane];
+    }
+    __device__ __forceinline__ PT& g(int i) const {
+        return i == 0 ? reinterpret_cast<PT*>(blk + L::off_g0)[lane]
+                      : reinterpret_cast<PT*>(blk + L::off_pairs + (i - 1) * L::pair_slot)[2 * lane + 1];
+    }
+    __device__ __forceinline__ Real& chz() const { return reinterpret_cast<Real*>(blk + L::off_chi)[2 * lane]; }
+    __device__ __forceinline__ Real& chr() const { return reinterpret_cast<Real*>(blk + L::off_chi)[2 * lane + 1]; }
     __device__ __forceinline__ Real& p() const { return reinterpret_cast<Real*>(blk + L::off_p)[lane]; }
 };
 
-// A node's population slots addressed by one byte pointer (block + lane *
-// sizeof(PT)): every f_i, g_i of the node is that pointer plus a constant.
+// A node's direction pairs addressed by one byte pointer (block + lane *
+// sizeof(PT2)): the pair of every direction i = 1..8 is that pointer plus a
+// constant.
 template <class Codec>
 struct PtRef {
-    using PT = typename Codec::PT;
+    using PT2 = typename Codec::PT2;
     using L = Block<Codec>;
     unsigned char* q;
-    __device__ __forceinline__ PT& f(int i) const {
-        return *reinterpret_cast<PT*>(q + L::off_fq + (i - 1) * 32 * (int)sizeof(PT));
-    }
-    __device__ __forceinline__ PT& g(int i) const {
-        return *reinterpret_cast<PT*>(q + L::off_g + i * 32 * (int)sizeof(PT));
+    __device__ __forceinline__ PT2& pair(int i) const {
+        return *reinterpret_cast<PT2*>(q + L::off_pairs + (i - 1) * L::pair_slot);
     }
 };
 
@@ -246,7 +271,7 @@ struct CaseView {
     }
     __device__ __forceinline__ PtRef<Codec> out_pt(int loc) const {
         return PtRef<Codec>{out + (int64_t)(loc >> 5) * Block<Codec>::bytes +
-                            (loc & 31) * (int)sizeof(typename Codec::PT)};
+                            (loc & 31) * (int)sizeof(typename Codec::PT2)};
     }
 };
 

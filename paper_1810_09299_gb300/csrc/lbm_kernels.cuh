@@ -37,23 +37,19 @@ constexpr int step_min_blocks() {
                 : (BZ >= 16 ? 1 : (BZ >= 8 ? 3 : 6));
 }
 
-// Store one post-collision population pair (f_I, g_I) at its destination
-// node `dst` as direction `dir`, with the destination radius normalisation
-// wr / iw.  Returns f_I as the reader will decode it (for the mass ledger).
+// Store one post-collision population pair (f_I, g_I), I = 1..8, at its
+// destination node `dst` as direction `dir` (one vector store), with the
+// destination radius normalisation wr / iw.  Returns f_I as the reader will
+// decode it (for the mass ledger).
 template <class Codec, int I>
 __device__ __forceinline__ typename Codec::Real store_pair(const PtRef<Codec>& dst, int dir, typename Codec::Real wr,
                                                            typename Codec::Real iw, typename Codec::Real fpi,
                                                            typename Codec::Real gpi) {
-    typename Codec::Real stored = fpi;
-    if (I != 0) {
-        const auto e = Codec::enc_f(fpi, wr, iw);
-        if constexpr (Codec::kStreamStores) __stcs(&dst.f(dir), e);
-        else dst.f(dir) = e;
-        stored = Codec::dec_f(e, wr);
-    }
-    if constexpr (Codec::kStreamStores) __stcs(&dst.g(dir), Codec::enc_g(gpi, wr, iw));
-    else dst.g(dir) = Codec::enc_g(gpi, wr, iw);
-    return stored;
+    static_assert(I != 0, "the rest populations stay at their node");
+    const typename Codec::PT2 e = Codec::enc_pair(fpi, gpi, wr, iw);
+    if constexpr (Codec::kStreamStores) __stcs(&dst.pair(dir), e);
+    else dst.pair(dir) = e;
+    return Codec::dec_f(e.x, wr);
 }
 
 // Steps a4-a10 for one node whose raw stored values have been fetched: decode,
@@ -110,8 +106,7 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     // destination slots of the fast path: the node's own population pointer
     // plus a row step and a lane step (which crosses into the next or the
     // previous block at lanes 31 and 0)
-    using PT = typename Codec::PT;
-    constexpr int kB = Block<Codec>::bytes, kPS = (int)sizeof(PT);
+    constexpr int kB = Block<Codec>::bytes, kPS = (int)sizeof(typename Codec::PT2);
     const int lane = loc & 31;
     unsigned char* const q0 = V.out_pt(loc).q;
     const int row = (C.pitch >> 5) * kB;
@@ -125,7 +120,13 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     if (!AXILBM_SPECIAL(I))                                                                                        \
         fs[I] = store_pair<Codec, I>(AXILBM_DST(I), I, (Real)w_of(I) * rdst[cr_of(I) + 1],                        \
                                      (Real)(1.0 / w_of(I)) * rinv[cr_of(I) + 1], fp[I], gp[I]);
-    AXILBM_PUSH_FAST(0)
+    // the rest direction: g_0 stays at the node (f_0 is written below)
+    {
+        const typename Codec::PT e0 = Codec::enc_g(gp[0], (Real)w_of(0) * r, (Real)(1.0 / w_of(0)) * m.inv_r);
+        if constexpr (Codec::kStreamStores) __stcs(&own.g(0), e0);
+        else own.g(0) = e0;
+        fs[0] = fp[0];
+    }
     AXILBM_PUSH_FAST(1)
     AXILBM_PUSH_FAST(2)
     AXILBM_PUSH_FAST(3)
@@ -219,9 +220,12 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
         const Node<Codec> n = V.in_node(loc);
         f0raw = n.f0();
 #pragma unroll
-        for (int i = 1; i < 9; ++i) fraw[i - 1] = n.f(i);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) graw[i] = n.g(i);
+        for (int i = 1; i < 9; ++i) {
+            const typename Codec::PT2 pr = n.pair(i);  // (f_i, g_i) in one load
+            fraw[i - 1] = pr.x;
+            graw[i] = pr.y;
+        }
+        graw[0] = n.g(0);
         chz_prev = n.chz();
         chr_prev = n.chr();
         if (C.p_coupling == 1) p_prev = n.p();
