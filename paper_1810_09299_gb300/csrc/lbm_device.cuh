@@ -536,12 +536,15 @@ __device__ __forceinline__ void inverse_moments_fg(const float* mf, const float*
 // S^f = diag(1, 1, 1, s, s, s, s, 1, 1) and S^g = 1 except s1 = s7 = s8 =
 // 1/tau_g(x) -- is known at compile time, so unit-rate moments go straight to
 // their equilibrium and s_p = (s1 + s2 - s1 s2) / (2 s1 s2) = tau_g / 2.
+//
+// inv_r_tab: when not null, 1 / r of the node's column (a table lookup
+// standing for the same correctly rounded quotient).
 template <typename Real, int LD, bool PR = false>
 __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, int a, int b, int j, const Real* mg,
-                                            Real g0, Real p_prev, Macro<Real>& m) {
+                                            Real g0, Real p_prev, Macro<Real>& m, const Real* inv_r_tab = nullptr) {
     const CaseReal<Real>& P = case_params<Real>(C);
     m.r = (Real)j + (Real)0.5;
-    m.inv_r = rcp_(m.r);
+    m.inv_r = inv_r_tab ? *inv_r_tab : rcp_(m.r);
     m.phi = sphi[a * LD + b];
     stencil<Real, LD>(sphi, a, b, m.gz, m.gr, m.lap);
     const Real rho_l = P.rho_l, rho_g = P.rho_g;

@@ -54,12 +54,15 @@ __device__ __forceinline__ typename Codec::Real store_pair(const PtRef<Codec>& d
 
 // Steps a4-a10 for one node whose raw stored values have been fetched: decode,
 // macroscopic recovery, both collisions, and the push with the boundary rules.
+// invr: when not null, 1 / r of window column b - 1, b, b + 1 at invr[b - 1 ..
+// b + 1] (the same quotients the node would compute itself).
 template <class Codec, bool PR, int LD>
 __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Codec>& V, const typename Codec::Real* sphi,
                                             int a, int b, int k, int j, int loc,
                                             const typename Codec::F0T& f0raw, const typename Codec::PT* fraw,
                                             const typename Codec::PT* graw, typename Codec::Real chz_prev,
-                                            typename Codec::Real chr_prev, typename Codec::Real p_prev) {
+                                            typename Codec::Real chr_prev, typename Codec::Real p_prev,
+                                            const typename Codec::Real* invr = nullptr) {
     using Real = typename Codec::Real;
     const Real r = (Real)j + (Real)0.5;
     Real f[9];
@@ -72,7 +75,7 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     Real mf[9], mg[9];
     moments_fg(f, g, mf, mg);
     Macro<Real> m;
-    node_macros<Real, LD, PR>(C, sphi, a, b, j, mg, g[0], p_prev, m);
+    node_macros<Real, LD, PR>(C, sphi, a, b, j, mg, g[0], p_prev, m, invr ? invr + b : nullptr);
     // mass ledger: two double-float lanes (f_0 and f_1..4; f_5..8) advanced
     // together; incoming total first, exact
     FF2 ledger{};
@@ -95,7 +98,8 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
 
     // 5. streaming (Eq. 20).  Rows j-1, j, j+1 are the only destinations, so
     //    three radii serve every normalisation.
-    const Real rinv[3] = {j > 0 ? rcp_(r - (Real)1) : (Real)0, m.inv_r, rcp_(r + (Real)1)};
+    const Real rinv[3] = {j > 0 ? (invr ? invr[b - 1] : rcp_(r - (Real)1)) : (Real)0, m.inv_r,
+                          invr ? invr[b + 1] : rcp_(r + (Real)1)};
     const Real rdst[3] = {r - (Real)1, r, r + (Real)1};
     // A link is special when it leaves the domain: through the axis, the wall
     // r = nr or a z boundary (wrap or bounce-back).  Every other link lands on
@@ -189,7 +193,16 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     // there, the collision's many per-case constants need no global loads.
     __shared__ __align__(16) CaseDev sC;
     static_assert(sizeof(CaseDev) % 4 == 0 && sizeof(CaseDev) / 4 <= kTR * BZ, "one word per thread");
+    // FP64: 1 / r of the window's columns j0 - 2 .. j0 + 33, one division per
+    // column instead of four per node (a division is a long sequence on the
+    // FP64 pipe); the same correctly rounded quotients the nodes would form
+    constexpr bool kInvrTable = sizeof(Real) == 8;
+    __shared__ Real s_invr[kInvrTable ? LD : 1];
     const TileDev t = tiles[blockIdx.x];
+    if constexpr (kInvrTable) {
+        const int q = threadIdx.y * kTR + threadIdx.x;
+        if (q < LD) s_invr[q] = (Real)1 / ((Real)(t.j0 - 2 + q) + (Real)0.5);
+    }
     // L2 prefetch of the blocks of the tile one resident wave ahead (a CTA
     // that will start about when this one ends): one tensor prefetch, issued
     // by one thread; the tensor maps are absent when they could not be made
@@ -260,7 +273,7 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
             f[i] = Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
             sum += f[i];
         }
-        sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = sum * rcp_(r);
+        sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = sum * (kInvrTable ? s_invr[threadIdx.x + 2] : rcp_(r));
     } else {
         sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = window_phi<Codec>(C, V, t, threadIdx.y + 2, threadIdx.x + 2);
     }
@@ -268,7 +281,7 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     if (!inside) return;
 
     node_update<Codec, PR, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw, graw, chz_prev,
-                               chr_prev, p_prev);
+                               chr_prev, p_prev, kInvrTable ? s_invr : nullptr);
 }
 
 // Shared-memory layout of one stage of the TMA-pipelined step for tile
