@@ -53,7 +53,7 @@ TRAFFIC_B_PER_NODE = {("fp32", 0): 164.77}
 # instructions (DADD + DFMA + DMUL) per node update from one ncu capture
 # (profiles/step_kernel_fp64_batched64cases.md), against the pipe's peak of
 # 2 per SM per cycle x 152 SMs x 2.07 GHz (maximum SM clock).
-FP64_OPS_PER_NODE = 403.3
+FP64_OPS_PER_NODE = 394.2
 FP64_PIPE_PEAK_GOPS = 2 * 152 * 2.07
 # What the GPU parity tests hold each precision to against the FP64 oracle.
 PARITY_TOL = {
@@ -419,7 +419,7 @@ def batched_other(torch, args, prec, steps):
         gops = FP64_OPS_PER_NODE * nodes / (ms * 1e-3) / 1e9
         out["alu_roofline"] = {"bound": "alu", "achieved": gops, "peak": FP64_PIPE_PEAK_GOPS,
                                "unit": "G FP64-pipe instructions/s", "frac": gops / FP64_PIPE_PEAK_GOPS,
-                               "note": "403 DADD+DFMA+DMUL per node (ncu); peak 2/SM/cycle x 152 SMs x 2.07 GHz"}
+                               "note": "394 DADD+DFMA+DMUL per node (ncu); peak 2/SM/cycle x 152 SMs x 2.07 GHz"}
     return out
 
 
