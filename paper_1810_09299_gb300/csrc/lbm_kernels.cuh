@@ -27,6 +27,26 @@ __device__ __forceinline__ typename Codec::Real window_phi(const CaseDev& C, con
     return node_phi<Codec>(V, k * C.pitch + j, r, rcp_(r));
 }
 
+// The ring of a tile's phi window: the two rows above and below the tile and
+// the two columns left and right of it, 4 * 32 + 4 * (TZ + 4) cells.  Cell q
+// maps to window position (a, b): first the 32 middle cells of each of the
+// four halo rows (one warp per row, lane = column, so a warp's loads are one
+// coalesced run and its ghost row is warp-uniform), then the two edge cells on
+// each side of every window row.
+template <int TZ>
+__device__ __forceinline__ void ring_cell(int q, int& a, int& b) {
+    if (q < 4 * kTR) {
+        const int w = q / kTR;
+        a = w < 2 ? w : TZ + w;
+        b = 2 + q % kTR;
+    } else {
+        const int q2 = q - 4 * kTR;
+        a = q2 >> 2;
+        const int c = q2 & 3;
+        b = c < 2 ? c : kTR + c;
+    }
+}
+
 // Minimum resident CTAs per SM requested from the register allocator: 32 warps
 // per SM (64 registers) for the FP32-arithmetic kernels with the paper's rate
 // pattern, which fit without spilling; 24 warps for general rates.
@@ -37,19 +57,41 @@ constexpr int step_min_blocks() {
                 : (BZ >= 16 ? 1 : (BZ >= 8 ? 3 : 6));
 }
 
-// Store one post-collision population pair (f_I, g_I), I = 1..8, at its
-// destination node `dst` as direction `dir` (one vector store), with the
-// destination radius normalisation wr / iw.  Returns f_I as the reader will
-// decode it (for the mass ledger).
-template <class Codec, int I>
-__device__ __forceinline__ typename Codec::Real store_pair(const PtRef<Codec>& dst, int dir, typename Codec::Real wr,
+// Store one post-collision population pair (f_i, g_i) in the slot `dst` of
+// its destination (one vector store), with the destination radius
+// normalisation wr / iw.  Returns f_i as the reader will decode it (for the
+// mass ledger).
+template <class Codec>
+__device__ __forceinline__ typename Codec::Real store_pair(typename Codec::PT2* dst, typename Codec::Real wr,
                                                            typename Codec::Real iw, typename Codec::Real fpi,
                                                            typename Codec::Real gpi) {
-    static_assert(I != 0, "the rest populations stay at their node");
     const typename Codec::PT2 e = Codec::enc_pair(fpi, gpi, wr, iw);
-    if constexpr (Codec::kStreamStores) __stcs(&dst.pair(dir), e);
-    else dst.pair(dir) = e;
+    if constexpr (Codec::kStreamStores) __stcs(dst, e);
+    else *dst = e;
     return Codec::dec_f(e.x, wr);
+}
+
+// Byte offset of direction d's pair slot inside a node group's block.
+template <class Codec>
+__device__ __forceinline__ constexpr int pair_slot_of(int d) {
+    return Block<Codec>::off_pairs + (d - 1) * Block<Codec>::pair_slot;
+}
+
+// Where the post-collision pair I of a node lands, as a byte offset from the
+// node's own pair pointer, for a node outside the z-wall rows: along c_i to
+// its neighbour (rz and the lane steps: the z row step, already wrapped for
+// periodic z, and the step to the next or previous lane, which crosses into
+// the adjacent block at lanes 31 and 0); through the wall r = nr back to the
+// node itself as direction opp(I); through the axis into row 0 of the
+// destination z row as the r-mirrored direction (Sec. 2.3).
+template <class Codec, int I>
+__device__ __forceinline__ int push_offset(bool axis, bool wall, int rowp, int rowm, int step_r, int step_l) {
+    static_assert(I != 0, "the rest populations stay at their node");
+    constexpr int cz = cz_of(I), cr = cr_of(I);
+    const int rz = cz > 0 ? rowp : (cz < 0 ? rowm : 0);
+    if constexpr (cr > 0) return wall ? pair_slot_of<Codec>(opp_of(I)) : rz + step_r + pair_slot_of<Codec>(I);
+    else if constexpr (cr < 0) return rz + (axis ? pair_slot_of<Codec>(rmir_of(I)) : step_l + pair_slot_of<Codec>(I));
+    else return rz + pair_slot_of<Codec>(I);
 }
 
 // Steps a4-a10 for one node whose raw stored values have been fetched: decode,
@@ -94,60 +136,35 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     collide_g<Real, PR>(C, m, mpg);
     Real fp[9], gp[9];
     inverse_moments_fg(mpf, mpg, fp, gp);
-    Real fs[9];  // f+ as stored, decoded
-
     // 5. streaming (Eq. 20).  Rows j-1, j, j+1 are the only destinations, so
-    //    three radii serve every normalisation.
-    const Real rinv[3] = {j > 0 ? (invr ? invr[b - 1] : rcp_(r - (Real)1)) : (Real)0, m.inv_r,
-                          invr ? invr[b + 1] : rcp_(r + (Real)1)};
-    const Real rdst[3] = {r - (Real)1, r, r + (Real)1};
-    // A link is special when it leaves the domain: through the axis, the wall
-    // r = nr or a z boundary (wrap or bounce-back).  Every other link lands on
-    // its neighbour and is stored by the branch-free fast path; the node's
-    // special links (at most 5) are then stored by the rules of destination().
-    // A warp that holds one boundary lane thus diverges only over those links.
+    //    three radii serve every normalisation.  On the axis every link with
+    //    c_r < 0 ends in the node's own row (mirror) or at the node itself
+    //    (bounce-back), and on the wall r = nr every link with c_r > 0 returns
+    //    to the node, so there the row's own radius takes the place of the
+    //    missing neighbour row.
     const bool axis = (j == 0), wall = (j + 1 == C.nr), zlo = (k == 0), zhi = (k + 1 == C.nz);
-    // destination slots of the fast path: the node's own population pointer
-    // plus a row step and a lane step (which crosses into the next or the
-    // previous block at lanes 31 and 0)
-    constexpr int kB = Block<Codec>::bytes, kPS = (int)sizeof(typename Codec::PT2);
+    const Real rinv[3] = {axis ? m.inv_r : (invr ? invr[b - 1] : rcp_(r - (Real)1)), m.inv_r,
+                          wall ? m.inv_r : (invr ? invr[b + 1] : rcp_(r + (Real)1))};
+    const Real rdst[3] = {axis ? r : r - (Real)1, r, wall ? r : r + (Real)1};
+    using PT2 = typename Codec::PT2;
+    constexpr int kB = Block<Codec>::bytes, kPS = (int)sizeof(PT2);
     const int lane = loc & 31;
-    unsigned char* const q0 = V.out_pt(loc).q;
-    const int row = (C.pitch >> 5) * kB;
+    unsigned char* const q0 = V.out_pt(loc).q;  // the node's own pair pointer
+    const int row = (C.pitch >> 5) * kB;         // one z row of blocks
     const int step_r = lane == 31 ? kB - 31 * kPS : kPS;
     const int step_l = lane == 0 ? -(kB - 31 * kPS) : -kPS;
-#define AXILBM_DST(I) \
-    PtRef<Codec>{q0 + (cz_of(I) * row + (cr_of(I) > 0 ? step_r : (cr_of(I) < 0 ? step_l : 0)))}
-#define AXILBM_SPECIAL(I) \
-    ((cr_of(I) < 0 && axis) || (cr_of(I) > 0 && wall) || (cz_of(I) < 0 && zlo) || (cz_of(I) > 0 && zhi))
-#define AXILBM_PUSH_FAST(I)                                                                                        \
-    if (!AXILBM_SPECIAL(I))                                                                                        \
-        fs[I] = store_pair<Codec, I>(AXILBM_DST(I), I, (Real)w_of(I) * rdst[cr_of(I) + 1],                        \
-                                     (Real)(1.0 / w_of(I)) * rinv[cr_of(I) + 1], fp[I], gp[I]);
-    // the rest direction: g_0 stays at the node (f_0 is written below)
-    {
-        const typename Codec::PT e0 = Codec::enc_g(gp[0], (Real)w_of(0) * r, (Real)(1.0 / w_of(0)) * m.inv_r);
-        if constexpr (Codec::kStreamStores) __stcs(&own.g(0), e0);
-        else own.g(0) = e0;
-        fs[0] = fp[0];
-    }
-    AXILBM_PUSH_FAST(1)
-    AXILBM_PUSH_FAST(2)
-    AXILBM_PUSH_FAST(3)
-    AXILBM_PUSH_FAST(4)
-    AXILBM_PUSH_FAST(5)
-    AXILBM_PUSH_FAST(6)
-    AXILBM_PUSH_FAST(7)
-    AXILBM_PUSH_FAST(8)
-#undef AXILBM_PUSH_FAST
-    if (axis || wall || zlo || zhi) {
-        // wrap, bounce-back or axis reflection (the rest direction is never special)
-#define AXILBM_PUSH(I)                                                                         \
-    if (AXILBM_SPECIAL(I)) {                                                                   \
-        const Dest d = destination<I>(k, j, C.nr, C.nz, C.zper);                               \
-        const int s = d.j - j + 1;                                                             \
-        fs[I] = store_pair<Codec, I>(V.out_pt(d.k * C.pitch + d.j), d.dir, (Real)w_of(I) * rdst[s], \
-                                     (Real)(1.0 / w_of(I)) * rinv[s], fp[I], gp[I]);                \
+    if ((zlo || zhi) && !C.zper) {
+        // A z-wall row (the whole warp: a warp is one row of a tile): every
+        // link by the rules of destination().
+        Real fs[9];
+#define AXILBM_PUSH(I)                                                                                 \
+    {                                                                                                  \
+        const Dest d = destination<I>(k, j, C.nr, C.nz, C.zper);                                       \
+        const int s = d.j - j + 1;                                                                     \
+        const Real rd = s == 0 ? rdst[0] : (s == 1 ? rdst[1] : rdst[2]);                               \
+        const Real ri = s == 0 ? rinv[0] : (s == 1 ? rinv[1] : rinv[2]);                               \
+        fs[I] = store_pair<Codec>(&V.out_pt(d.k * C.pitch + d.j).pair(d.dir), (Real)w_of(I) * rd,      \
+                                  (Real)(1.0 / w_of(I)) * ri, fp[I], gp[I]);                           \
     }
         AXILBM_PUSH(1)
         AXILBM_PUSH(2)
@@ -158,14 +175,42 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
         AXILBM_PUSH(7)
         AXILBM_PUSH(8)
 #undef AXILBM_PUSH
+        if constexpr (Codec::kLedger) {
+#pragma unroll
+            for (int i = 1; i < 5; ++i) ff2_sub(ledger, make_float2((float)fs[i], (float)fs[i + 4]));
+        }
+    } else {
+        // Every other node, branch-free: the axis and wall lanes differ from
+        // their warp only in the offsets of push_offset(), and a z row that
+        // wraps (periodic z) only in its row steps.  The ledger takes each
+        // pair of directions (i, i + 4) as soon as both are stored.
+        const int rowp = zhi ? -(C.nz - 1) * row : row;
+        const int rowm = zlo ? (C.nz - 1) * row : -row;
+#define AXILBM_STORE(I)                                                                                      \
+    store_pair<Codec>(                                                                                       \
+        reinterpret_cast<PT2*>(q0 + push_offset<Codec, I>(axis, wall, rowp, rowm, step_r, step_l)),          \
+        (Real)w_of(I) * rdst[cr_of(I) + 1], (Real)(1.0 / w_of(I)) * rinv[cr_of(I) + 1], fp[I], gp[I])
+#define AXILBM_STORE_TWO(I)                                                                  \
+    {                                                                                        \
+        const Real fa = AXILBM_STORE(I), fb = AXILBM_STORE(I + 4);                           \
+        if constexpr (Codec::kLedger) ff2_sub(ledger, make_float2((float)fa, (float)fb));    \
     }
-#undef AXILBM_SPECIAL
-#undef AXILBM_DST
+        AXILBM_STORE_TWO(1)
+        AXILBM_STORE_TWO(2)
+        AXILBM_STORE_TWO(3)
+        AXILBM_STORE_TWO(4)
+#undef AXILBM_STORE_TWO
+#undef AXILBM_STORE
+    }
+    // the rest direction: g_0 stays at the node
+    {
+        const typename Codec::PT e0 = Codec::enc_g(gp[0], (Real)w_of(0) * r, (Real)(1.0 / w_of(0)) * m.inv_r);
+        if constexpr (Codec::kStreamStores) __stcs(&own.g(0), e0);
+        else own.g(0) = e0;
+    }
     // f_0: the collision's value (FP64), or the mass ledger: incoming total
     // minus the outgoing f_1..8 as they will be read back
     if constexpr (Codec::kLedger) {
-#pragma unroll
-        for (int i = 1; i < 5; ++i) ff2_sub(ledger, make_float2((float)fs[i], (float)fs[i + 4]));
         const FF l = ff2_merge(ledger);
         own.f0() = make_float2(l.hi, l.lo);
     } else {
@@ -187,7 +232,8 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     using F0T = typename Codec::F0T;
     constexpr int TZ = BZ;
     constexpr int LD = kTR + 4;
-    constexpr int NRING = 4 * LD + 4 * TZ;
+    constexpr int NRING = 4 * kTR + 4 * (TZ + 4);
+    static_assert(NRING == (TZ + 4) * LD - TZ * kTR, "the ring is the window without the tile");
     __shared__ Real sphi[(TZ + 4) * LD];
     // The case's parameters are copied to shared memory first: read from
     // there, the collision's many per-case constants need no global loads.
@@ -247,19 +293,7 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     //    left and right of the tile)
     for (int q = threadIdx.y * kTR + threadIdx.x; q < NRING; q += kTR * BZ) {
         int a, b;
-        if (q < 2 * LD) {
-            a = q / LD;
-            b = q - a * LD;
-        } else if (q < 4 * LD) {
-            const int q2 = q - 2 * LD;
-            a = TZ + 2 + q2 / LD;
-            b = q2 - (q2 / LD) * LD;
-        } else {
-            const int q3 = q - 4 * LD;
-            const int c = q3 / TZ;
-            a = 2 + (q3 - c * TZ);
-            b = c < 2 ? c : kTR + c;
-        }
+        ring_cell<TZ>(q, a, b);
         sphi[a * LD + b] = window_phi<Codec>(C, V, t, a, b);
     }
     // 3. the node's own phi (Eq. 16); window cells outside the domain take the ghost rule
@@ -384,7 +418,8 @@ step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
     using F0T = typename Codec::F0T;
     using L = TmaTile<Codec, BZ>;
     constexpr int TZ = BZ, LD = L::LD, NS = L::NS;
-    constexpr int NRING = 4 * LD + 4 * TZ;
+    constexpr int NRING = 4 * kTR + 4 * (TZ + 4);
+    static_assert(NRING == (TZ + 4) * LD - TZ * kTR, "the ring is the window without the tile");
     constexpr int kWaitTries = 1 << 22;
     extern __shared__ __align__(128) unsigned char smem[];
     Real* sphi = (Real*)(smem + L::off_phi);  // [HR][LD]
@@ -445,19 +480,7 @@ step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
         // the ring of the phi window, from the staged box
         for (int q = tid; q < NRING; q += kTR * BZ) {
             int a, b;
-            if (q < 2 * LD) {
-                a = q / LD;
-                b = q - a * LD;
-            } else if (q < 4 * LD) {
-                const int q2 = q - 2 * LD;
-                a = TZ + 2 + q2 / LD;
-                b = q2 - (q2 / LD) * LD;
-            } else {
-                const int q3 = q - 4 * LD;
-                const int c = q3 / TZ;
-                a = 2 + (q3 - c * TZ);
-                b = c < 2 ? c : kTR + c;
-            }
+            ring_cell<TZ>(q, a, b);
             sphi[a * LD + b] = staged_phi<Codec, TZ>(st, C, V, tt, a, b);
         }
         // the node's own phi (Eq. 16) from its staged populations
