@@ -346,25 +346,27 @@ struct Macro {
     Real mg[9];  // M g (hydrodynamic moments before collision)
 };
 
-// Stencils (Eq. 39, Eq. 40) from the shared phi window centred on (cz0, cr0).
+// Stencils (Eq. 39, Eq. 40) from the shared phi window centred on (a, b).
+// With x1, x2 the values one and two links along c_i, d_i = 8 x1 - x2 and
+// u_i = 16 x1 - x2:
+//   grad phi = sum_i w_i c_i d_i / (6 cs^2),
+//   lap phi  = (sum_i w_i u_i - 15 phi sum_i w_i) / (6 cs^2),
+// with 6 cs^2 = 2 and sum_{i>0} w_i = 5/9, the sums grouped by weight class.
 template <typename Real, int LD>
 __device__ __forceinline__ void stencil(const Real* sphi, int a, int b, Real& gz, Real& gr, Real& lap) {
     const Real c0 = sphi[a * LD + b];
-    Real sz = 0, sr = 0, sl = 0;
+    Real d[9], u[9];
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         const Real x1 = sphi[(a + cz_of(i)) * LD + (b + cr_of(i))];
         const Real x2 = sphi[(a + 2 * cz_of(i)) * LD + (b + 2 * cr_of(i))];
-        const Real w = (Real)w_of(i);
-        const Real d = (Real)8 * x1 - x2;
-        if (cz_of(i) != 0) sz += (Real)cz_of(i) * w * d;
-        if (cr_of(i) != 0) sr += (Real)cr_of(i) * w * d;
-        sl += w * ((Real)16 * x1 - x2 - (Real)15 * c0);
+        d[i] = (Real)8 * x1 - x2;
+        u[i] = (Real)8 * x1 + d[i];
     }
-    // divide by 6 cs^2 = 2
-    gz = sz * (Real)0.5;
-    gr = sr * (Real)0.5;
-    lap = sl * (Real)0.5;
+    const Real h1 = (Real)(1.0 / 18.0), h2 = (Real)(1.0 / 72.0);  // w_i / 2 on the axes and diagonals
+    gz = h1 * (d[1] - d[3]) + h2 * ((d[5] + d[8]) - (d[6] + d[7]));
+    gr = h1 * (d[2] - d[4]) + h2 * ((d[5] + d[6]) - (d[7] + d[8]));
+    lap = h1 * ((u[1] + u[2]) + (u[3] + u[4])) + h2 * ((u[5] + u[6]) + (u[7] + u[8])) - (Real)(25.0 / 6.0) * c0;
 }
 
 // M g for the nine hydrodynamic populations (rows of M in Sec. 2.2).
