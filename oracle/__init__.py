@@ -29,7 +29,7 @@ Q = 9
 class OrcParams(ctypes.Structure):
     _fields_ = [
         ("nr", ctypes.c_int32), ("nz", ctypes.c_int32), ("z_periodic", ctypes.c_int32),
-        ("p_coupling", ctypes.c_int32),
+        ("p_coupling", ctypes.c_int32), ("collision", ctypes.c_int32),
         ("rho_l", ctypes.c_double), ("rho_g", ctypes.c_double),
         ("nu_l", ctypes.c_double), ("nu_g", ctypes.c_double),
         ("sigma", ctypes.c_double), ("W", ctypes.c_double),
@@ -88,6 +88,9 @@ def lib():
             L.orc_lattice.argtypes = [ip, ip, dp]
             L.orc_matrix_M.argtypes = [dp]
             L.orc_matrix_Minv.argtypes = [dp]
+            L.orc_matrix_T.argtypes = [dp]
+            L.orc_matrix_Tinv.argtypes = [dp]
+            L.orc_raw_collide.argtypes = [dp, dp, dp, dp, dp]
             L.orc_feq.argtypes = [ctypes.c_double] * 5 + [dp]
             L.orc_R.argtypes = [ctypes.c_double] * 6 + [dp]
             L.orc_geq.argtypes = [ctypes.c_double] * 5 + [dp]
@@ -112,6 +115,7 @@ def make_params(case: dict) -> OrcParams:
     p.nr, p.nz = int(case["nr"]), int(case["nz"])
     p.z_periodic = int(case.get("z_periodic", 0))
     p.p_coupling = int(case.get("p_coupling", 0))
+    p.collision = int(case.get("collision", 0))
     for k in ("rho_l", "rho_g", "nu_l", "nu_g", "sigma", "W", "mobility"):
         setattr(p, k, float(case[k]))
     p.grav_z = float(case.get("grav_z", 0.0))
@@ -143,6 +147,19 @@ def matrix_Minv() -> np.ndarray:
     return out.reshape(9, 9)
 
 
+def matrix_T() -> np.ndarray:
+    """The raw-moment basis (rows 1, c_z, c_r, c^2, c_z^2 - c_r^2, c_z c_r, c_z^2 c_r, c_z c_r^2, c_z^2 c_r^2)."""
+    out = np.zeros(81)
+    lib().orc_matrix_T(_p(out))
+    return out.reshape(9, 9)
+
+
+def matrix_Tinv() -> np.ndarray:
+    out = np.zeros(81)
+    lib().orc_matrix_Tinv(_p(out))
+    return out.reshape(9, 9)
+
+
 def feq(r, phi, uz, ur, mobility) -> np.ndarray:
     out = np.zeros(9)
     lib().orc_feq(r, phi, uz, ur, mobility, _p(out))
@@ -171,6 +188,14 @@ def mrt_collide(x, xeq, src, S) -> np.ndarray:
     x, xeq, src, S = _c(x), _c(xeq), _c(src), _c(S)
     out = np.zeros(9)
     lib().orc_mrt_collide(_p(x), _p(xeq), _p(src), _p(S), _p(out))
+    return out
+
+
+def raw_collide(x, xeq, src, S) -> np.ndarray:
+    """The collision of mrt_collide in the raw-moment basis (S: rates of the raw moments)."""
+    x, xeq, src, S = _c(x), _c(xeq), _c(src), _c(S)
+    out = np.zeros(9)
+    lib().orc_raw_collide(_p(x), _p(xeq), _p(src), _p(S), _p(out))
     return out
 
 

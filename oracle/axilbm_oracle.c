@@ -23,6 +23,11 @@
  * d(r rho) taken analytically from grad(phi), halfway mirror ghosts, axis
  * specular reflection, corner links bounced back, G = ((rho-rho_l) g_z, 0),
  * initial state f = f^eq(phi0, 0), g = 0, chi^{-1} = chi^0, p^{-1} = 0.
+ *
+ * Option: the non-orthogonal (raw-moment) MRT that the paper's summary
+ * (Sec. 4) names as a direct extension -- the same Eq. 10 / Eq. 24 collisions
+ * with M replaced by the raw-moment basis, and s_p of Eq. 33 re-derived for it
+ * (see node_macros).
  */
 #include "axilbm_oracle.h"
 
@@ -42,6 +47,7 @@ static const double CS2 = 1.0 / 3.0; /* c_s^2 = c^2/3 with c = 1 (Eq. 12) */
 static int g_cz[Q], g_cr[Q];
 static double g_w[Q];
 static double g_M[Q * Q], g_Minv[Q * Q];
+static double g_T[Q * Q], g_Tinv[Q * Q];
 static int g_opp[Q], g_rmirror[Q];
 static int g_ready = 0;
 
@@ -116,12 +122,28 @@ static void invert9(const double* A, double* Ainv)
         for (int j = 0; j < Q; ++j) Ainv[i * Q + j] = a[i][Q + j];
 }
 
+/* The non-orthogonal (raw-moment) basis that the paper's summary (Sec. 4)
+ * names as the direct extension of its orthogonal MRT: row k holds the
+ * polynomial p_k(c) at every lattice vector, with
+ *   p = 1, c_z, c_r, c_z^2 + c_r^2, c_z^2 - c_r^2, c_z c_r, c_z^2 c_r, c_z c_r^2,
+ *       c_z^2 c_r^2. */
+static void build_raw_basis(void)
+{
+    for (int i = 0; i < Q; ++i) {
+        const double z = g_cz[i], r = g_cr[i];
+        const double row[Q] = {1.0, z, r, z * z + r * r, z * z - r * r, z * r, z * z * r, z * r * r, z * z * r * r};
+        for (int k = 0; k < Q; ++k) g_T[k * Q + i] = row[k];
+    }
+}
+
 static void ensure_tables(void)
 {
     if (g_ready) return;
     build_lattice();
     memcpy(g_M, M_PAPER, sizeof(g_M));
     invert9(g_M, g_Minv);
+    build_raw_basis();
+    invert9(g_T, g_Tinv);
     g_ready = 1;
 }
 
@@ -192,22 +214,39 @@ void orc_T(double rho, double uz, double ur, double Fz, double Fr,
     }
 }
 
-/* Eq. 19 with Eq. 10 and Eq. 14 (and the same form, Eq. 24 + Eq. 27, for g):
- * x+ = x - M^-1 S M (x - xeq) + M^-1 (I - S/2) M src.
+/* Eq. 19 with Eq. 10 and Eq. 14 (and the same form, Eq. 24 + Eq. 27, for g)
+ * in the moment basis B:
+ * x+ = x - B^-1 S B (x - xeq) + B^-1 (I - S/2) B src.
  * The matrix products are applied right to left to the vectors. */
+static void collide_in_basis(const double* B, const double* Binv, const double* x, const double* xeq,
+                             const double* src, const double* S, double* xpost)
+{
+    double d[Q], md[Q], ms[Q], msrc[Q], back1[Q], back2[Q];
+    for (int i = 0; i < Q; ++i) d[i] = x[i] - xeq[i];
+    matvec9(B, d, md);
+    for (int i = 0; i < Q; ++i) md[i] *= S[i];
+    matvec9(Binv, md, back1);
+    matvec9(B, src, msrc);
+    for (int i = 0; i < Q; ++i) ms[i] = (1.0 - 0.5 * S[i]) * msrc[i];
+    matvec9(Binv, ms, back2);
+    for (int i = 0; i < Q; ++i) xpost[i] = x[i] - back1[i] + back2[i];
+}
+
+/* the paper's orthogonal MRT: B = M of Sec. 2.2 */
 void orc_mrt_collide(const double* x, const double* xeq, const double* src, const double* S,
                      double* xpost)
 {
     ensure_tables();
-    double d[Q], md[Q], ms[Q], msrc[Q], back1[Q], back2[Q];
-    for (int i = 0; i < Q; ++i) d[i] = x[i] - xeq[i];
-    matvec9(g_M, d, md);
-    for (int i = 0; i < Q; ++i) md[i] *= S[i];
-    matvec9(g_Minv, md, back1);
-    matvec9(g_M, src, msrc);
-    for (int i = 0; i < Q; ++i) ms[i] = (1.0 - 0.5 * S[i]) * msrc[i];
-    matvec9(g_Minv, ms, back2);
-    for (int i = 0; i < Q; ++i) xpost[i] = x[i] - back1[i] + back2[i];
+    collide_in_basis(g_M, g_Minv, x, xeq, src, S, xpost);
+}
+
+/* the raw-moment (non-orthogonal) MRT: B = the raw basis above, S the rates of
+ * its nine moments */
+void orc_raw_collide(const double* x, const double* xeq, const double* src, const double* S,
+                     double* xpost)
+{
+    ensure_tables();
+    collide_in_basis(g_T, g_Tinv, x, xeq, src, S, xpost);
 }
 
 /* ------------------------------------------------------------------ */
@@ -287,6 +326,8 @@ void orc_lattice(int* cz, int* cr, double* w)
 }
 void orc_matrix_M(double* M) { ensure_tables(); memcpy(M, g_M, sizeof(g_M)); }
 void orc_matrix_Minv(double* Minv) { ensure_tables(); memcpy(Minv, g_Minv, sizeof(g_Minv)); }
+void orc_matrix_T(double* T) { ensure_tables(); memcpy(T, g_T, sizeof(g_T)); }
+void orc_matrix_Tinv(double* Tinv) { ensure_tables(); memcpy(Tinv, g_Tinv, sizeof(g_Tinv)); }
 
 void orc_set_threads(int nthreads)
 {
@@ -426,7 +467,14 @@ static void node_macros(const orc_state* s, int k, int j, node_macro* m)
     }
     double drho = P->rho_l - P->rho_g;
     double dzrho = drho * m->dphiz, drrho = drho * m->dphir;
-    double sp = (m->sg[1] + m->sg[2] - m->sg[1] * m->sg[2]) / (2.0 * m->sg[1] * m->sg[2]);
+    /* s_p of Eq. 33 (Appendix C).  In the raw basis the i = 0 row of
+     * T^-1 S^-1 T takes raw moments 0, 3 and 8 (x_0 = k_0 - k_3 + k_8), and the
+     * appendix's argument, with the moments of its Eq. C.7 matched term by term,
+     * gives s_p = 3 / (2 s_3) - 1 / (2 s_8) - 1/2 (equal to the orthogonal s_p
+     * whenever the two collisions coincide, e.g. for a single rate). */
+    double sp = (P->collision == 1)
+                    ? 1.5 / m->sg[3] - 0.5 / m->sg[8] - 0.5
+                    : (m->sg[1] + m->sg[2] - m->sg[1] * m->sg[2]) / (2.0 * m->sg[1] * m->sg[2]);
     double w0 = g_w[0];
     /* Eq. 32, z component (independent of p) */
     m->uz = (Jz + 0.5 * r * (m->Fsz + m->Gz)) / (r * m->rho);
@@ -486,7 +534,8 @@ int orc_step(orc_state* s, int64_t nsteps)
                 double chiz = r * m.phi * m.uz;
                 double chir = r * m.phi * m.ur + P->mobility * m.phi;
                 orc_R(r, chiz - s->chi_z[n], chir - s->chi_r[n], m.nz_, m.nr_, m.lam, R);
-                orc_mrt_collide(f, feq, R, m.sf, fpost);
+                if (P->collision == 1) orc_raw_collide(f, feq, R, m.sf, fpost);
+                else orc_mrt_collide(f, feq, R, m.sf, fpost);
                 /* ---- hydrodynamic LBE: Eq. 24 with Eq. 25-30 ---- */
                 double g[Q], geq[Q], T[Q], gpost[Q];
                 for (int i = 0; i < Q; ++i) g[i] = s->g[i * N + n];
@@ -495,7 +544,8 @@ int orc_step(orc_state* s, int64_t nsteps)
                 double dz_rrho = r * drho * m.dphiz;            /* d_z (r rho) */
                 double dr_rrho = m.rho + r * drho * m.dphir;    /* d_r (r rho) */
                 orc_T(m.rho, m.uz, m.ur, m.Fz, m.Fr, dz_rrho, dr_rrho, T);
-                orc_mrt_collide(g, geq, T, m.sg, gpost);
+                if (P->collision == 1) orc_raw_collide(g, geq, T, m.sg, gpost);
+                else orc_mrt_collide(g, geq, T, m.sg, gpost);
                 /* time-level bookkeeping for Eq. 38 and the lagged p */
                 s->chi_z[n] = chiz;
                 s->chi_r[n] = chir;

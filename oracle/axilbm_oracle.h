@@ -32,10 +32,16 @@ extern "C" {
  * p_coupling: 0 = node-local exact solve of Eq. 32 + Eq. 33 for (u, p)
  *                 (p appears in u_r and u in p; the pair is a quadratic in p);
  *             1 = lagged pressure p^{n-1} in Eq. 32 and Eq. 30.
- * n_eps: n = grad(phi) / (|grad(phi)| + n_eps). */
+ * n_eps: n = grad(phi) / (|grad(phi)| + n_eps).
+ * collision: 0 = the paper's orthogonal MRT (M of Sec. 2.2);
+ *            1 = raw-moment MRT: M replaced by the non-orthogonal basis
+ *                1, c_z, c_r, c_z^2 + c_r^2, c_z^2 - c_r^2, c_z c_r, c_z^2 c_r,
+ *                c_z c_r^2, c_z^2 c_r^2 (the extension named in Sec. 4); sf / sg
+ *                are then the rates of these moments. */
 typedef struct {
     int32_t nr, nz, z_periodic;
     int32_t p_coupling;
+    int32_t collision;
     double rho_l, rho_g, nu_l, nu_g, sigma, W, mobility, grav_z;
     double sf[9], sg[9];
     double n_eps;
@@ -76,6 +82,8 @@ void orc_set_threads(int nthreads);
 void orc_lattice(int* cz, int* cr, double* w);          /* 9 each */
 void orc_matrix_M(double* M);                           /* 81, row-major */
 void orc_matrix_Minv(double* Minv);                     /* 81, Gauss-Jordan inverse of M */
+void orc_matrix_T(double* T);                           /* 81, raw-moment basis */
+void orc_matrix_Tinv(double* Tinv);                     /* 81, Gauss-Jordan inverse of T */
 /* Eq. 11 */
 void orc_feq(double r, double phi, double uz, double ur, double mobility, double* feq);
 /* Eq. 15 */
@@ -87,6 +95,9 @@ void orc_T(double rho, double uz, double ur, double Fz, double Fr,
            double dz_rrho, double dr_rrho, double* T);
 /* Eq. 10 + Eq. 14 / Eq. 24 + Eq. 27: x+ = x - M^-1 S M (x - xeq) + M^-1 (I - S/2) M src */
 void orc_mrt_collide(const double* x, const double* xeq, const double* src, const double* S,
+                     double* xpost);
+/* the same with the raw-moment basis T in place of M */
+void orc_raw_collide(const double* x, const double* xeq, const double* src, const double* S,
                      double* xpost);
 /* Eq. 39 and Eq. 40 on an arbitrary [nz][nr] field with the ghost rules of Sec. 2.3 */
 void orc_stencil(int nr, int nz, int z_periodic, const double* field,

@@ -30,6 +30,14 @@ CS2 = 1.0 / 3.0
 SF_PAPER = (1.0, 1.0, 1.0, -1.0, -1.0, -1.0, -1.0, 1.0, 1.0)
 SG_PAPER = (1.0, -1.0, 1.0, 1.0, 1.0, 1.0, 1.0, -1.0, -1.0)
 
+# The same rate choice for the raw-moment collision (collision = 1), whose
+# moments are 1, c_z, c_r, c_z^2 + c_r^2, c_z^2 - c_r^2, c_z c_r, c_z^2 c_r,
+# c_z c_r^2, c_z^2 c_r^2: for f the first and third moments relax with
+# 1/tau_f; for g the three second moments relax with 1/tau_g.
+SF_RAW_PAPER = (1.0, -1.0, -1.0, 1.0, 1.0, 1.0, -1.0, -1.0, 1.0)
+SG_RAW_PAPER = (1.0, 1.0, 1.0, -1.0, -1.0, -1.0, 1.0, 1.0, 1.0)
+COLLISIONS = {"orthogonal": 0, "raw": 1}
+
 PRECISIONS = {"fp64": 0, "fp32": 1, "mix_fp16": 2, "mix_bf16": 3}
 
 
@@ -99,10 +107,17 @@ def phi_from_shape(nz, nr, shape: str, args):
 
 # ------------------------------------------------------------------ cases
 def base_case(**kw) -> dict:
-    c = dict(nr=16, nz=32, z_periodic=0, p_coupling=0, precision="fp64",
+    c = dict(nr=16, nz=32, z_periodic=0, p_coupling=0, collision=0, precision="fp64",
              rho_l=1.0, rho_g=1e-3, nu_l=0.1, nu_g=0.1, sigma=0.01, W=4.0,
              mobility=0.1, grav_z=0.0, sf=list(SF_PAPER), sg=list(SG_PAPER), n_eps=1e-12)
     c.update(kw)
+    return c
+
+
+def with_raw_collision(case: dict) -> dict:
+    """The case with the raw-moment collision and the paper's rate choice in that basis."""
+    c = dict(case)
+    c.update(collision=1, sf=list(SF_RAW_PAPER), sg=list(SG_RAW_PAPER))
     return c
 
 

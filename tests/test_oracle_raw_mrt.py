@@ -1,0 +1,166 @@
+"""Pins of the oracle's raw-moment (non-orthogonal) MRT option (CPU).
+
+The paper's summary (Sec. 4) names the non-orthogonal MRT as a direct
+extension of its orthogonal model.  The option keeps the collisions of
+Eq. 10 / Eq. 24 and replaces M by the raw-moment basis 1, c_z, c_r,
+c_z^2 + c_r^2, c_z^2 - c_r^2, c_z c_r, c_z^2 c_r, c_z c_r^2, c_z^2 c_r^2.
+What fixes it independently of the oracle's own code:
+- the raw moments of f^eq (Eq. 11) have closed forms from the lattice sums
+  sum w_i = 1, sum w_i c_a c_b = cs2 delta_ab, sum w_i c_z^2 c_r^2 = 1/9;
+- a diagonal rate matrix acts the same in any basis whose rows span the same
+  subspaces per rate: with rate s on {c_z, c_r, c_z^2 c_r, c_z c_r^2} and 1
+  elsewhere the raw collision is the paper's f-collision (rate s on j and q,
+  Sec. 2.2), since q_z = 3 c_z c_r^2 - 2 c_z and q_r = 3 c_z^2 c_r - 2 c_r;
+- a single rate is BGK in every basis (Sec. 2.2), so a single-rate run is
+  the same in both bases, s_p of Eq. 33 included;
+- the whole scheme keeps Laplace's law and conserves mass.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import analytic as A
+from paper_1810_09299_gb300 import workloads as W
+
+RNG = np.random.default_rng(1810)
+
+
+def _rand(n):
+    return RNG.uniform(-1.0, 1.0, size=n)
+
+
+@pytest.mark.parametrize("trial", range(6))
+def test_raw_moments_of_feq_closed_form(trial):
+    r, phi = RNG.uniform(0.5, 40.0), RNG.uniform(-0.1, 1.1)
+    uz, ur, mob = _rand(1)[0] * 0.05, _rand(1)[0] * 0.05, RNG.uniform(0.01, 0.2)
+    k = oracle.matrix_T() @ oracle.feq(r, phi, uz, ur, mob)
+    chi_z, chi_r = r * phi * uz, r * phi * ur + mob * phi
+    ref = [r * phi, chi_z, chi_r, 2.0 / 3.0 * r * phi, 0.0, 0.0, chi_r / 3.0, chi_z / 3.0, r * phi / 9.0]
+    assert np.allclose(k, ref, rtol=0, atol=1e-13 * max(1.0, r))
+
+
+def test_raw_basis_inverse():
+    T, Ti = oracle.matrix_T(), oracle.matrix_Tinv()
+    assert np.max(np.abs(Ti @ T - np.eye(9))) < 1e-14
+    # the rest population is k_0 - k_3 + k_8 (the i = 0 row of T^-1 used for s_p)
+    assert np.allclose(Ti[0], [1, 0, 0, -1, 0, 0, 0, 0, 1], atol=1e-15)
+
+
+@pytest.mark.parametrize("s", [0.55, 1.0, 1.3, 1.85])
+def test_raw_with_paper_f_rates_is_the_orthogonal_f_collision(s):
+    x, xeq, src = _rand(9), _rand(9), 0.1 * _rand(9)
+    raw = oracle.raw_collide(x, xeq, src, np.array([1, s, s, 1, 1, 1, s, s, 1.0]))
+    ortho = oracle.mrt_collide(x, xeq, src, np.array([1, 1, 1, s, s, s, s, 1, 1.0]))
+    assert np.max(np.abs(raw - ortho)) <= 1e-13 * np.max(np.abs(ortho))
+
+
+@pytest.mark.parametrize("s", [0.6, 1.0, 1.7])
+def test_raw_with_a_single_rate_is_bgk(s):
+    x, xeq, src = _rand(9), _rand(9), 0.1 * _rand(9)
+    got = oracle.raw_collide(x, xeq, src, np.full(9, s))
+    bgk = x - s * (x - xeq) + (1 - s / 2) * src
+    assert np.max(np.abs(got - bgk)) <= 1e-14 * np.max(np.abs(bgk))
+
+
+def test_raw_g_collision_is_a_different_operator():
+    """With the paper's g rates (second moments at 1/tau_g) the raw basis does
+    not span the orthogonal rate subspaces (e = 3 c^2 - 4 mixes the zeroth moment
+    in), so the two hydrodynamic collisions differ."""
+    s = 1.0 / 0.8
+    x, xeq, src = _rand(9), _rand(9), 0.1 * _rand(9)
+    raw = oracle.raw_collide(x, xeq, src, np.array([1, 1, 1, s, s, s, 1, 1, 1.0]))
+    ortho = oracle.mrt_collide(x, xeq, src, np.array([1, s, 1, 1, 1, 1, 1, s, s]))
+    assert np.max(np.abs(raw - ortho)) > 1e-3
+    # both keep the same momentum (rate 1 on c_z, c_r in both)
+    T = oracle.matrix_T()
+    assert np.allclose((T @ raw)[1:3], (T @ ortho)[1:3], atol=1e-14)
+
+
+def _single_rate_case(collision, z_periodic):
+    c = W.static_drop(nr=20, nz=32, R=7.0, ratio=10.0, z_periodic=z_periodic, grav_z=-1e-5)
+    c.update(collision=collision, sf=[-1.0] * 9, sg=[-1.0] * 9)
+    return c
+
+
+@pytest.mark.parametrize("zper", [0, 1])
+def test_single_rate_runs_agree_in_both_bases(zper):
+    """Single-rate f and g (BGK with the local 1/tau_g): the raw and orthogonal
+    runs are the same scheme, s_p of Eq. 33 included (both give 1/s - 1/2)."""
+    out = []
+    for coll in (0, 1):
+        case = _single_rate_case(coll, zper)
+        o = oracle.Oracle(case).init(W.initial_phi(case))
+        o.step(150)
+        out.append(o.fields())
+    for k in ("phi", "uz", "ur", "p"):
+        scale = max(1e-12, np.max(np.abs(out[0][k])))
+        assert np.max(np.abs(out[1][k] - out[0][k])) <= 1e-11 * scale, k
+
+
+@pytest.mark.parametrize("zper", [0, 1])
+def test_raw_mass_conserved_to_roundoff(zper):
+    case = W.with_raw_collision(W.static_drop(nr=20, nz=32, R=7.0, z_periodic=zper, ratio=10.0, grav_z=-1e-5))
+    o = oracle.Oracle(case).init(W.initial_phi(case))
+    m0 = o.diagnostics()["mass"]
+    o.step(300)
+    assert abs(o.diagnostics()["mass"] - m0) <= 1e-13 * m0
+
+
+def test_raw_laplace_law_static_drop():
+    """The raw-moment scheme on the static drop (64 x 128, R = 16, ratio 1000):
+    Laplace's law within 1 % with R_eff from the drop volume.  4000 steps: at
+    2000 the drop is still ringing in both bases (|u|max about 8e-3), the
+    orthogonal run 0.5 % and the raw one 1.4 % from the law; at 4000 both are
+    within 0.15 %."""
+    case = W.with_raw_collision(W.static_drop())
+    o = oracle.Oracle(case).init(W.initial_phi(case))
+    m0 = o.diagnostics()["mass"]
+    o.step(4000)
+    d = o.diagnostics()
+    F = o.fields()
+    r = np.arange(case["nr"])[None, :] + 0.5
+    V = 2 * math.pi * np.sum(r * F["phi"])
+    R_eff = (3 * V / (4 * math.pi)) ** (1 / 3)
+    dp_th = A.laplace_jump(case["sigma"], R_eff)
+    assert abs(d["dp"] - dp_th) / dp_th < 0.01, (d["dp"], dp_th)
+    assert abs(d["mass"] - m0) / m0 < 1e-12
+
+
+def test_raw_hagen_poiseuille_pipe_flow():
+    """Shear rates in the raw basis: uniform gas in a pipe of radius nr, periodic
+    in z, driven by G_z.  u_z(r) = G (R^2 - r^2) / (4 rho nu) within 1 %, which
+    holds only if the three second raw moments relax with 1/tau_g (Eq. 34)."""
+    nr, nu, rho = 16, 0.1, 1.0
+    c = W.with_raw_collision(W.base_case(nr=nr, nz=4, z_periodic=1, rho_l=2.0, rho_g=rho, nu_l=nu, nu_g=nu,
+                                         sigma=0.0, mobility=0.1, grav_z=-1e-5))
+    o = oracle.Oracle(c).init(np.zeros((4, nr)))
+    o.step(15000)
+    F = o.fields()
+    r = np.arange(nr) + 0.5
+    G = (rho - 2.0) * -1e-5
+    ex = G * (nr ** 2 - r ** 2) / (4 * rho * nu)
+    assert np.max(np.abs(F["uz"][0] - ex)) / ex.max() < 0.01
+    assert np.max(np.abs(F["ur"])) < 1e-3 * ex.max()
+
+
+def test_raw_oscillating_drop_frequency_miller_scriven():
+    """The n = 2 oscillation of a P2-deformed drop in the raw scheme within 10 %
+    of Eq. 43, as the orthogonal scheme (reduced grid 60 x 120, R0 = 20)."""
+    pytest.importorskip("scipy")
+    from tests.test_oracle_pins import _fit_frequency
+    case = W.with_raw_collision(W.oscillating_drop(nr=60, nz=120, R0=20.0, eps=0.1, sigma=0.01))
+    o = oracle.Oracle(case).init(W.initial_phi(case))
+    Re = (3 * o.diagnostics()["mass"] * 2 * math.pi / (4 * math.pi)) ** (1 / 3)
+    ts, L = [], []
+    for _ in range(200):
+        o.step(25)
+        ts.append(o.steps)
+        L.append(o.diagnostics()["axis_half_length"])
+    ts, L = np.array(ts, float), np.array(L)
+    w_th = A.miller_scriven_frequency(2, Re, case["rho_l"], case["rho_g"], case["nu_l"], case["nu_g"],
+                                      case["sigma"])
+    sel = ts > 300
+    w = _fit_frequency(ts[sel], L[sel], w_th)
+    assert abs(w - w_th) / w_th < 0.10, (w, w_th)
