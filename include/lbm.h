@@ -66,6 +66,20 @@ typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_MIX_FP16 = 2, LBM_MIX_BF16 = 3 } 
  * LBM_P_LAGGED uses p^{n-1} in Eq. 32 and Eq. 30. */
 typedef enum { LBM_P_EXACT = 0, LBM_P_LAGGED = 1 } lbm_p_coupling;
 
+/* Moment basis of both collisions (Eq. 19 and Eq. 24).
+ *   LBM_MRT_ORTHOGONAL  the paper's orthogonal moments, M of Sec. 2.2.
+ *   LBM_MRT_RAW         the non-orthogonal raw moments 1, c_z, c_r, c_z^2 + c_r^2,
+ *                       c_z^2 - c_r^2, c_z c_r, c_z^2 c_r, c_z c_r^2, c_z^2 c_r^2: the
+ *                       extension the paper's summary names (Sec. 4).  sf and sg
+ *                       then give the rates of these nine moments, and s_p of
+ *                       Eq. 33 becomes 3 / (2 s_3) - 1 / (2 s_8) - 1/2 (Appendix C
+ *                       redone in this basis).  The paper's rate choice reads
+ *                       sf = (1, s, s, 1, 1, 1, s, s, 1), for which the f-collision
+ *                       is the paper's own, and sg = 1 except s_3 = s_4 = s_5 =
+ *                       1/tau_g.  Cases with this basis run the general-rate
+ *                       kernels. */
+typedef enum { LBM_MRT_ORTHOGONAL = 0, LBM_MRT_RAW = 1 } lbm_collision;
+
 /* Parameters of one case.
  *   nr, nz       lattice size (nr >= 2, nz >= 2).
  *   z_periodic   1: periodic in z; 0: halfway bounce-back walls at z = 0 and z = nz.
@@ -81,12 +95,13 @@ typedef enum { LBM_P_EXACT = 0, LBM_P_LAGGED = 1 } lbm_p_coupling;
  *                negative entry is derived: sf -> 1/tau_f, sg -> 1/tau_g(x) with
  *                nu(x) = cs2 (tau_g - 1/2) at every node (Eq. 34).
  *   n_eps        interface normal n = grad phi / (|grad phi| + n_eps).
- *   precision    lbm_precision; p_coupling lbm_p_coupling. */
+ *   precision    lbm_precision; p_coupling lbm_p_coupling; collision
+ *                lbm_collision. */
 typedef struct {
     int32_t nr, nz, z_periodic;
     int32_t precision;
     int32_t p_coupling;
-    int32_t reserved;
+    int32_t collision;
     double rho_l, rho_g, nu_l, nu_g, sigma, W, mobility, grav_z;
     double sf[9], sg[9];
     double n_eps;

@@ -43,6 +43,7 @@ int validate(const lbm_params& p) {
     if (p.z_periodic != 0 && p.z_periodic != 1) return LBM_ERR_INVALID_ARG;
     if (p.precision < LBM_FP64 || p.precision > LBM_MIX_BF16) return LBM_ERR_INVALID_ARG;
     if (p.p_coupling != LBM_P_EXACT && p.p_coupling != LBM_P_LAGGED) return LBM_ERR_INVALID_ARG;
+    if (p.collision != LBM_MRT_ORTHOGONAL && p.collision != LBM_MRT_RAW) return LBM_ERR_INVALID_ARG;
     if (!finite_pos(p.rho_l) || !finite_pos(p.rho_g) || !finite_pos(p.nu_l) || !finite_pos(p.nu_g))
         return LBM_ERR_INVALID_ARG;
     if (!finite_pos(p.W) || !finite_pos(p.mobility)) return LBM_ERR_INVALID_ARG;
@@ -222,6 +223,7 @@ void fill_params(CaseReal<Real>& P, const lbm_params& p) {
 // s, 1, 1) with one s; S^g = 1 except s1 = s7 = s8 derived from the local
 // viscosity.
 bool paper_rate_pattern(const lbm_params& p) {
+    if (p.collision != LBM_MRT_ORTHOGONAL) return false;
     for (int i : {0, 1, 2, 7, 8})
         if (p.sf[i] != 1.0) return false;
     for (int i = 4; i <= 6; ++i)
@@ -241,6 +243,7 @@ CaseDev make_case(const lbm_params& p, int64_t off) {
     C.plane = p.nz * C.pitch;
     C.zper = p.z_periodic;
     C.p_coupling = p.p_coupling;
+    C.collision = p.collision;
     C.off = off;
     C.sg_local = 0;
     for (int i = 0; i < 9; ++i)

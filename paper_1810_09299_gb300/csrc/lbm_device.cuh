@@ -61,7 +61,7 @@ struct CaseDev {
     uint32_t sg_local;  // bit i set: sg[i] = 1/tau_g(x) from the local viscosity (Eq. 34)
     int64_t off;        // node offset of the case (see above)
     int32_t plane;      // nz * pitch
-    int32_t pad1;
+    int32_t collision;  // 0: orthogonal moments (M, Sec. 2.2); 1: raw moments (see raw_from_ortho)
     CaseReal<double> pd;
     CaseReal<float> pf;
     int32_t pad2[2];    // size a multiple of 16 bytes (bulk-copyable)
@@ -413,6 +413,54 @@ __device__ __forceinline__ void inverse_moments(const Real* m, Real* x) {
     x[8] = d + qz - qr - a8;
 }
 
+// ---------------------------------------------------------------- raw moments
+// The non-orthogonal basis of the raw-moment collision (the extension named
+// in Sec. 4): k_0..8 = sums of x_i times 1, c_z, c_r, c_z^2 + c_r^2,
+// c_z^2 - c_r^2, c_z c_r, c_z^2 c_r, c_z c_r^2, c_z^2 c_r^2.  On D2Q9 each is a
+// fixed combination of the orthogonal moments of M (c^2 = (e + 4) / 3,
+// c_z c_r^2 = (q_z + 2 j_z) / 3, c_z^2 c_r^2 = (eps + 2 e + 4) / 9, ...), so
+// the collision stays in the orthogonal moments the step already has and maps
+// the deviations into the raw basis and back.
+template <typename Real>
+__device__ __forceinline__ void raw_from_ortho(const Real* m, Real* k) {
+    k[0] = m[0];
+    k[1] = m[3];
+    k[2] = m[5];
+    k[3] = (m[1] + (Real)4 * m[0]) * (Real)(1.0 / 3.0);
+    k[4] = m[7];
+    k[5] = m[8];
+    k[6] = (m[6] + (Real)2 * m[5]) * (Real)(1.0 / 3.0);
+    k[7] = (m[4] + (Real)2 * m[3]) * (Real)(1.0 / 3.0);
+    k[8] = (m[2] + (Real)2 * m[1] + (Real)4 * m[0]) * (Real)(1.0 / 9.0);
+}
+template <typename Real>
+__device__ __forceinline__ void ortho_from_raw(const Real* k, Real* m) {
+    m[0] = k[0];
+    m[3] = k[1];
+    m[5] = k[2];
+    m[1] = (Real)3 * k[3] - (Real)4 * k[0];
+    m[7] = k[4];
+    m[8] = k[5];
+    m[6] = (Real)3 * k[6] - (Real)2 * k[2];
+    m[4] = (Real)3 * k[7] - (Real)2 * k[1];
+    m[2] = (Real)9 * k[8] - (Real)6 * k[3] + (Real)4 * k[0];
+}
+// m+ = m - A^-1 S A (m - meq) + A^-1 (I - S/2) A src, A = raw_from_ortho: the
+// collision of Eq. 10 / Eq. 24 with S the rates of the raw moments.
+template <typename Real>
+__device__ __forceinline__ void raw_relax(const Real* m, const Real* meq, const Real* src, const Real* s, Real* mp) {
+    Real d[9], dk[9], sk[9], dm[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = m[i] - meq[i];
+    raw_from_ortho(d, dk);
+    raw_from_ortho(src, sk);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) dk[i] = -s[i] * dk[i] + ((Real)1 - (Real)0.5 * s[i]) * sk[i];
+    ortho_from_raw(dk, dm);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) mp[i] = m[i] + dm[i];
+}
+
 // ---------------------------------------------------------------- paired FP32 transforms
 // The two LBEs apply the same moment matrix to their nine populations.  In
 // FP32 the pair (f_i, g_i) is held as one float2 and transformed with the
@@ -580,6 +628,9 @@ __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, 
     Real sp;
     if constexpr (PR) {
         sp = (Real)0.5 * tau_g;
+    } else if (C.collision == 1) {
+        // raw moments: Appendix C in that basis (x_0 = k_0 - k_3 + k_8)
+        sp = (Real)1.5 * rcp_(m.sg[3]) - (Real)0.5 * rcp_(m.sg[8]) - (Real)0.5;
     } else {
         const Real s1 = m.sg[1], s2 = m.sg[2];
         sp = div_(s1 + s2 - s1 * s2, (Real)2 * s1 * s2);
@@ -637,6 +688,8 @@ __device__ __forceinline__ void collide_f(const CaseDev& C, const Macro<Real>& m
         for (int k = 3; k < 7; ++k) mp[k] = mf[k] - s * (mf[k] - meq[k]) + h * mR[k];
         mp[7] = (Real)0;
         mp[8] = (Real)0;
+    } else if (C.collision == 1) {
+        raw_relax<Real>(mf, meq, mR, P.sf, mp);
     } else {
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -676,6 +729,8 @@ __device__ __forceinline__ void collide_g(const CaseDev& C, const Macro<Real>& m
             if (k == 1 || k == 7 || k == 8) mp[k] = m.mg[k] - s * (m.mg[k] - meq[k]) + h * MT[k];
             else mp[k] = meq[k] + (Real)0.5 * MT[k];
         }
+    } else if (C.collision == 1) {
+        raw_relax<Real>(m.mg, meq, MT, m.sg, mp);
     } else {
 #pragma unroll
         for (int k = 0; k < 9; ++k) {

@@ -44,7 +44,7 @@ DIAG_SLOTS = 4
 class LbmParams(ctypes.Structure):
     _fields_ = [
         ("nr", ctypes.c_int32), ("nz", ctypes.c_int32), ("z_periodic", ctypes.c_int32),
-        ("precision", ctypes.c_int32), ("p_coupling", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("p_coupling", ctypes.c_int32), ("collision", ctypes.c_int32),
         ("rho_l", ctypes.c_double), ("rho_g", ctypes.c_double),
         ("nu_l", ctypes.c_double), ("nu_g", ctypes.c_double),
         ("sigma", ctypes.c_double), ("W", ctypes.c_double),
@@ -138,6 +138,7 @@ def make_params(case: dict) -> LbmParams:
     prec = case.get("precision", "fp64")
     p.precision = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     p.p_coupling = int(case.get("p_coupling", 0))
+    p.collision = int(case.get("collision", 0))
     for k in ("rho_l", "rho_g", "nu_l", "nu_g", "sigma", "W", "mobility"):
         setattr(p, k, float(case[k]))
     p.grav_z = float(case.get("grav_z", 0.0))
