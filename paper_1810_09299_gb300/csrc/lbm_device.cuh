@@ -132,6 +132,37 @@ struct CodecF32 {
     __device__ static PT2 enc_pair(Real f, Real g, Real, Real) { return make_float2(f, g); }
 };
 
+// Mixed-precision adds (PTX ISA 8.6, sm_100 family): the 16-bit operand is
+// converted exactly and added to the FP32 one with one rounding, the same
+// result as a conversion followed by an FP32 add (checked bit for bit over
+// every FP16 value on the GPU), in one instruction.
+__device__ __forceinline__ float add_h(__half h, float c) {
+    float d;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(__half_as_ushort(h)), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float add_h(__nv_bfloat16 h, float c) {
+    float d;
+    asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(__bfloat16_as_ushort(h)), "f"(c));
+    return d;
+}
+
+// phi of a node (Eq. 16) from its raw stored f_0 and f_1..8: sum f_i / r.
+// With the 16-bit decode f_i = (h_i + 1/2) w_i r the sum reads
+//   phi = f_0 / r + (h_1 + .. + h_4 + 2) / 9 + (h_5 + .. + h_8 + 2) / 36,
+// summed from the stored values with eight mixed-precision adds (no decode);
+// every path that forms phi of a 16-bit node uses this one form, so the phi
+// window is the same whichever tile or launch shape computes a cell.
+template <typename PT>
+__device__ __forceinline__ float phi_from_halves(float f0, const PT* h, float inv_r) {
+    float a = 2.0f, b = 2.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a = add_h(h[i], a);
+#pragma unroll
+    for (int i = 4; i < 8; ++i) b = add_h(h[i], b);
+    return __fmaf_rn(f0, inv_r, __fmaf_rn(a, 1.0f / 9.0f, b * (1.0f / 36.0f)));
+}
+
 // kStreamStores: the step writes its pushed populations with evict-first
 // stores (measured: -1.5 % on the 16-bit step, +2.8 % on the FP32 one).
 //
@@ -306,17 +337,44 @@ __device__ __forceinline__ int ghost_z(int k, int nz, int zper) {
     return min(max(k, 0), nz - 1);
 }
 
-// phi at an in-domain node from its stored populations (Eq. 16).
+// phi of a node from its raw stored f_0 (F0T) and f_1..8 (Eq. 16): the
+// plain sum in FP64 and FP32 storage, phi_from_halves in 16-bit storage.
+template <class Codec>
+__device__ __forceinline__ typename Codec::Real phi_of(const typename Codec::F0T& f0raw,
+                                                        const typename Codec::PT* fraw,
+                                                        typename Codec::Real inv_r) {
+    using Real = typename Codec::Real;
+    if constexpr (sizeof(typename Codec::PT) == 2) {
+        return phi_from_halves(f0_value(f0raw), fraw, inv_r);
+    } else {
+        Real s = (Real)f0_value(f0raw);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) s += fraw[i];
+        return s * inv_r;
+    }
+}
+
+// phi at an in-domain node from its stored populations (Eq. 16).  FP64 and
+// FP32: each load feeds the running sum (the order phi_of sums in).
+template <class Codec>
+__device__ __forceinline__ typename Codec::Real node_phi(const Node<Codec>& n, typename Codec::Real inv_r) {
+    using Real = typename Codec::Real;
+    if constexpr (sizeof(typename Codec::PT) == 2) {
+        typename Codec::PT fraw[8];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) fraw[i - 1] = n.f(i);
+        return phi_of<Codec>(n.f0(), fraw, inv_r);
+    } else {
+        Real s = (Real)f0_value(n.f0());
+#pragma unroll
+        for (int i = 1; i < 9; ++i) s += n.f(i);
+        return s * inv_r;
+    }
+}
 template <class Codec>
 __device__ __forceinline__ typename Codec::Real node_phi(const CaseView<Codec>& V, int loc,
-                                                          typename Codec::Real r,
                                                           typename Codec::Real inv_r) {
-    using Real = typename Codec::Real;
-    const Node<Codec> n = V.in_node(loc);
-    Real s = (Real)f0_value(n.f0());
-#pragma unroll
-    for (int i = 1; i < 9; ++i) s += Codec::dec_f(n.f(i), (Real)w_of(i) * r);
-    return s * inv_r;
+    return node_phi<Codec>(V.in_node(loc), inv_r);
 }
 
 // ---------------------------------------------------------------- arithmetic helpers

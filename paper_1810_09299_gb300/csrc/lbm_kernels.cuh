@@ -24,7 +24,7 @@ __device__ __forceinline__ typename Codec::Real window_phi(const CaseDev& C, con
     const int k = ghost_z(t.k0 - 2 + a, C.nz, C.zper);
     const int j = ghost_r(t.j0 - 2 + b, C.nr);
     const Real r = (Real)j + (Real)0.5;
-    return node_phi<Codec>(V, k * C.pitch + j, r, rcp_(r));
+    return node_phi<Codec>(V, k * C.pitch + j, rcp_(r));
 }
 
 // The ring of a tile's phi window: the two rows above and below the tile and
@@ -329,6 +329,10 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     // 3. the node's own phi (Eq. 16); window cells outside the domain take the ghost rule
     const Real r = (Real)j + (Real)0.5;
     Real f[9];
+    // 16-bit storage: the decoded f live on across the barrier (measured
+    // -1.5 % against decoding them again; +0.6 % in FP32, where decoding is
+    // free)
+    constexpr bool kKeepF = sizeof(PT) == 2;
     if (inside) {
         f[0] = (Real)f0_value(f0raw);
         Real sum = f[0];
@@ -337,17 +341,16 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
             f[i] = Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
             sum += f[i];
         }
-        sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = sum * (kInvrTable ? s_invr[threadIdx.x + 2] : rcp_(r));
+        const Real inv_r = kInvrTable ? s_invr[threadIdx.x + 2] : rcp_(r);
+        // 16-bit storage: phi in the one form of phi_of (sum unused)
+        sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] =
+            kKeepF ? phi_of<Codec>(f0raw, fraw, inv_r) : sum * inv_r;
     } else {
         sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = window_phi<Codec>(C, V, t, threadIdx.y + 2, threadIdx.x + 2);
     }
     __syncthreads();
     if (!inside) return;
 
-    // 16-bit storage: the f decoded for phi live on across the barrier
-    // (measured -1.5 % against decoding them again; +0.6 % in FP32, where
-    // decoding is free)
-    constexpr bool kKeepF = sizeof(PT) == 2;
     node_update<Codec, PR, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw, graw, chz_prev,
                                chr_prev, p_prev, kInvrTable ? s_invr : nullptr, kKeepF ? f : nullptr);
 }
@@ -412,12 +415,9 @@ __device__ __forceinline__ typename Codec::Real staged_phi(const unsigned char* 
     const Real r = (Real)jm + (Real)0.5;
     if (sa >= 0 && sa < L::HR && (jm >> 5) == (tt.j0 >> 5)) {
         const Node<Codec> n{const_cast<unsigned char*>(st + L::off_box) + (size_t)sa * Block<Codec>::bytes, jm & 31};
-        Real sum = (Real)f0_value(n.f0());
-#pragma unroll
-        for (int i = 1; i < 9; ++i) sum += Codec::dec_f(n.f(i), (Real)w_of(i) * r);
-        return sum * rcp_(r);
+        return node_phi<Codec>(n, rcp_(r));
     }
-    return node_phi<Codec>(V, km * C.pitch + jm, r, rcp_(r));
+    return node_phi<Codec>(V, km * C.pitch + jm, rcp_(r));
 }
 
 // Resident CTAs per SM: as many as the stages' shared memory allows (up to
@@ -528,7 +528,8 @@ step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
                 f[i] = Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
                 sum += f[i];
             }
-            sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = sum * rcp_(r);
+            sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] =
+                sizeof(PT) == 2 ? phi_of<Codec>(f0raw, fraw, rcp_(r)) : sum * rcp_(r);
         } else {
             sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] =
                 staged_phi<Codec, TZ>(st, C, V, tt, threadIdx.y + 2, threadIdx.x + 2);
