@@ -164,3 +164,42 @@ def test_raw_oscillating_drop_frequency_miller_scriven():
     sel = ts > 300
     w = _fit_frequency(ts[sel], L[sel], w_th)
     assert abs(w - w_th) / w_th < 0.10, (w, w_th)
+
+
+def _stokes_cell(collision, n, A0=2e-3, T0=400):
+    """A decaying axisymmetric cellular flow of uniform gas with u_r != 0:
+    u from the Stokes stream function psi = A r^2 (R^2 - r^2)^2 sin(kz) / R^4
+    (no slip at the wall r = R = nr, periodic in z), g = g^eq(p = 0, rho, u).
+    Grid 24n x 48n, amplitude 1/n and T0 n^2 steps (diffusive scaling);
+    returns u_z averaged over n x n blocks, scaled back by n."""
+    nr, nz = 24 * n, 48 * n
+    R, k, A = float(nr), 2 * math.pi / nz, A0 / n
+    z = np.arange(nz)[:, None] + 0.5
+    r = np.arange(nr)[None, :] + 0.5
+    uz = A / R ** 4 * (2 * (R ** 2 - r ** 2) ** 2 - 4 * r ** 2 * (R ** 2 - r ** 2)) * np.sin(k * z)
+    ur = -A / R ** 4 * r * (R ** 2 - r ** 2) ** 2 * k * np.cos(k * z)
+    c = W.base_case(nr=nr, nz=nz, z_periodic=1, rho_l=1.0, rho_g=1.0, nu_l=0.1, nu_g=0.1, sigma=0.0,
+                    mobility=0.1)
+    if collision:
+        c = W.with_raw_collision(c)
+    o = oracle.Oracle(c).init(np.zeros((nz, nr)))
+    f, _ = o.populations()
+    g = np.zeros((9, nz, nr))
+    for kk in range(nz):
+        for j in range(nr):
+            g[:, kk, j] = oracle.geq(r[0, j], 0.0, 1.0, uz[kk, j], ur[kk, j])
+    o.set_populations(f, g)
+    o.step(T0 * n * n)
+    return o.fields()["uz"].reshape(48, n, 24, n).mean(axis=(1, 3)) * n
+
+
+def test_raw_and_orthogonal_velocities_converge_together():
+    """The two hydrodynamic collisions differ, but both must discretise the same
+    axisymmetric flow equations: in a flow with u_r != 0 their velocities must
+    approach each other under refinement (measured: 2.7 % of max |u_z| apart on
+    the 24 x 48 grid, 0.47 % on 48 x 96, 0.14 % on 72 x 144)."""
+    d = []
+    for n in (1, 2):
+        a, b = _stokes_cell(0, n), _stokes_cell(1, n)
+        d.append(np.max(np.abs(b - a)) / np.max(np.abs(a)))
+    assert d[0] < 0.05 and d[1] < 0.01 and d[1] < d[0] / 4, d
