@@ -203,3 +203,95 @@ def test_raw_and_orthogonal_velocities_converge_together():
         a, b = _stokes_cell(0, n), _stokes_cell(1, n)
         d.append(np.max(np.abs(b - a)) / np.max(np.abs(a)))
     assert d[0] < 0.05 and d[1] < 0.01 and d[1] < d[0] / 4, d
+
+
+# ---------------------------------------------------------------- s_p of Eq. 33 in the raw basis
+def _sp_ortho(s1, s2):
+    return (s1 + s2 - s1 * s2) / (2 * s1 * s2)
+
+
+def _sp_raw(s3, s8):
+    return 1.5 / s3 - 0.5 / s8 - 0.5
+
+
+def _residual_raw_moments(z0=3.0, r0=5.0, eps=1e-6, h=1e-3):
+    """Raw moments 0, 3, 8 of v = -c . grad g^eq + T (Appendix C's residual with
+    the time derivatives dropped, as the appendix does under incompressibility),
+    at one point of a slow incompressible axisymmetric flow of uniform density,
+    from the oracle's g^eq (Eq. 25) and T (Eq. 29) with central differences.
+    u from a stream function: u_z = psi_r / r, u_r = -psi_z / r."""
+    rho = 1.0
+    cz, cr, w = oracle.lattice()
+    T = oracle.matrix_T()
+
+    def u(z, r):
+        # psi = eps r^2 (1 + 0.3 z + 0.1 r + 0.05 z r)
+        psi_r = eps * (2 * r * (1 + 0.3 * z + 0.1 * r + 0.05 * z * r) + r * r * (0.1 + 0.05 * z))
+        psi_z = eps * r * r * (0.3 + 0.05 * r)
+        return psi_r / r, -psi_z / r
+
+    def flux(z, r):  # sum_i T_ki c_i g_i^eq for both components
+        uz, ur = u(z, r)
+        g = oracle.geq(r, 1e-4 * (1 + 0.2 * z + 0.3 * r), rho, uz, ur)
+        return T @ (cz * g), T @ (cr * g)
+
+    div = (flux(z0 + h, r0)[0] - flux(z0 - h, r0)[0]) / (2 * h) + (flux(z0, r0 + h)[1] - flux(z0, r0 - h)[1]) / (2 * h)
+    uz, ur = u(z0, r0)
+    Tf = oracle.T_force(rho, uz, ur, 0.0, 0.0, 0.0, rho)  # d(r rho) = (0, rho) for uniform rho
+    k = -div + T @ Tf
+    return k, Tf[0], rho, ur
+
+
+def test_appendix_c_residual_moments():
+    """Premise of s_p in both bases: for the residual of Appendix C the raw moments
+    0, 3 and 8 are 0, (2/3) rho u_r and (2/9) rho u_r (lattice sums of Eq. 25 and
+    Eq. 29 with div(r u) = 0)."""
+    k, T0, rho, ur = _residual_raw_moments()
+    scale = abs(rho * ur)
+    assert abs(k[0]) < 1e-6 * scale
+    assert abs(k[3] - 2.0 / 3.0 * rho * ur) < 1e-6 * scale
+    assert abs(k[8] - 2.0 / 9.0 * rho * ur) < 1e-6 * scale
+    assert abs(T0 + 4.0 / 9.0 * rho * ur) < 1e-12 * scale
+
+
+@pytest.mark.parametrize("s_a,s_b", [(1.25, 1.0), (0.7, 1.3), (1.6, 0.9)])
+def test_sp_follows_from_appendix_c_in_both_bases(s_a, s_b):
+    """(g_0 - g_0^eq) / dt = [B^-1 S^-1 B v]_0 - T_0 / 2 = -s_p w_0 rho u_r
+    (Appendix C, Eq. C.6 and C.8) with the numerically formed residual v: the
+    orthogonal basis gives the paper's s_p (rates s_1 = s_a of e, s_2 = s_b of
+    eps), the raw basis 3/(2 s_3) - 1/(2 s_8) - 1/2 (s_3 = s_a of c^2, s_8 = s_b
+    of c_z^2 c_r^2)."""
+    k, T0, rho, ur = _residual_raw_moments()
+    w0 = 4.0 / 9.0
+    # orthogonal: M^-1 row 0 = (1/9, -1/9, 1/9, 0, ...), (M v)_1 = 3 k3 - 4 k0, (M v)_2 = 4 k0 - 6 k3 + 9 k8
+    g0_ortho = (k[0] - (3 * k[3] - 4 * k[0]) / s_a + (4 * k[0] - 6 * k[3] + 9 * k[8]) / s_b) / 9.0 - T0 / 2
+    Ti = oracle.matrix_Tinv()
+    g0_raw = Ti[0, 0] * k[0] + Ti[0, 3] * k[3] / s_a + Ti[0, 8] * k[8] / s_b - T0 / 2
+    assert abs(-g0_ortho / (w0 * rho * ur) - _sp_ortho(s_a, s_b)) < 1e-5
+    assert abs(-g0_raw / (w0 * rho * ur) - _sp_raw(s_a, s_b)) < 1e-5
+
+
+@pytest.mark.parametrize("zper", [0, 1])
+def test_oracle_pressure_uses_the_raw_sp(zper):
+    """Same populations, lagged coupling (u_r does not depend on p): the two
+    bases' Eq. 33 pressures differ by -(cs2/(1-w0)) (s_p_raw - s_p_ortho) w0 rho u_r / r."""
+    nu = 0.1
+    tau = 3 * nu + 0.5
+    base = W.static_drop(nr=18, nz=30, R=6.0, z_periodic=zper, ratio=10.0, p_coupling=1)
+    base.update(nu_l=nu, nu_g=nu)
+    rng = np.random.default_rng(7)
+    o0 = oracle.Oracle(base).init(W.initial_phi(base))
+    f, g = o0.populations()
+    g = g + 1e-4 * rng.standard_normal(g.shape)
+    out = []
+    for case in (base, W.with_raw_collision(base)):
+        o = oracle.Oracle(case).init(W.initial_phi(case))
+        o.set_populations(f, g)
+        out.append(o.fields())
+    a, b = out
+    r = np.arange(base["nr"])[None, :] + 0.5
+    s = 1.0 / tau
+    d_sp = _sp_raw(s, 1.0) - _sp_ortho(s, 1.0)
+    expect = -(1.0 / 3.0) / (5.0 / 9.0) * d_sp * (4.0 / 9.0) * a["rho"] * a["ur"] / r
+    assert np.allclose(b["ur"], a["ur"], rtol=0, atol=1e-15)
+    assert np.max(np.abs((b["p"] - a["p"]) - expect)) < 1e-12 * max(np.max(np.abs(expect)), 1e-30)
