@@ -154,7 +154,8 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     node_pre<Codec>(f0raw, fraw, graw, r, P, fdec);
     const Real* mf = P.mf;
     Macro<Real> m;
-    node_macros<Real, LD, PR>(C, sphi, a, b, j, P.mg, P.g0, p_prev, m, invr ? invr + b : nullptr);
+    node_macros<Real, LD, PR, sizeof(typename Codec::PT) == 2>(C, sphi, a, b, j, P.mg, P.g0, p_prev, m,
+                                                               invr ? invr + b : nullptr);
     FF2 ledger = P.ledger;
     Real mpf[9], chz, chr;
     collide_f<Real, PR>(C, m, mf, chz_prev, chr_prev, chz, chr, mpf);
