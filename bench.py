@@ -48,12 +48,12 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf
 # launch; profiles/step_kernel_fp32_batched64cases.md), keyed by precision and
 # launch variant.  Scaled to a full launch by the node count.  Kept only for
 # the kernel build that was captured.
-TRAFFIC_B_PER_NODE = {("fp32", 0): 164.83}
+TRAFFIC_B_PER_NODE = {("fp32", 0): 164.86}
 # The FP64 step is bound by the FP64 pipe, not by HBM: FP64-pipe thread
 # instructions (DADD + DFMA + DMUL) per node update from one ncu capture
 # (profiles/step_kernel_fp64_batched64cases.md), against the pipe's peak of
 # 2 per SM per cycle x 152 SMs x 2.07 GHz (maximum SM clock).
-FP64_OPS_PER_NODE = 384.3
+FP64_OPS_PER_NODE = 383.3
 FP64_PIPE_PEAK_GOPS = 2 * 152 * 2.07
 # What the GPU parity tests hold each precision to against the FP64 oracle.
 PARITY_TOL = {
