@@ -323,7 +323,7 @@ def run_cuda(args):
     if rank == 0 and not args.no_extra:
         sim.close()
         if args.workload == "batched":
-            for other in ("fp32", "mix_fp16", "fp64"):
+            for other in ("fp32", "mix_fp16", "mix_bf16", "fp64"):
                 if other != prec:
                     line[f"batched_{other}"] = batched_other(torch, args, other, steps=min(args.steps, 50)
                                                              if other != "fp64" else 5)
@@ -419,7 +419,8 @@ def batched_other(torch, args, prec, steps):
         gops = FP64_OPS_PER_NODE * nodes / (ms * 1e-3) / 1e9
         out["alu_roofline"] = {"bound": "alu", "achieved": gops, "peak": FP64_PIPE_PEAK_GOPS,
                                "unit": "G FP64-pipe instructions/s", "frac": gops / FP64_PIPE_PEAK_GOPS,
-                               "note": "394 DADD+DFMA+DMUL per node (ncu); peak 2/SM/cycle x 152 SMs x 2.07 GHz"}
+                               "note": f"{FP64_OPS_PER_NODE} DADD+DFMA+DMUL per node (ncu); "
+                                       "peak 2/SM/cycle x 152 SMs x 2.07 GHz"}
     return out
 
 
