@@ -150,13 +150,13 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
                                             const typename Codec::Real* fdec = nullptr) {
     using Real = typename Codec::Real;
     const Real r = (Real)j + (Real)0.5;
-    PreCollision<Real> P;
-    node_pre<Codec>(f0raw, fraw, graw, r, P, fdec);
-    const Real* mf = P.mf;
+    PreCollision<Real> pre;
+    node_pre<Codec>(f0raw, fraw, graw, r, pre, fdec);
+    const Real* mf = pre.mf;
     Macro<Real> m;
-    node_macros<Real, LD, PR, sizeof(typename Codec::PT) == 2>(C, sphi, a, b, j, P.mg, P.g0, p_prev, m,
+    node_macros<Real, LD, PR, sizeof(typename Codec::PT) == 2>(C, sphi, a, b, j, pre.mg, pre.g0, p_prev, m,
                                                                invr ? invr + b : nullptr);
-    FF2 ledger = P.ledger;
+    FF2 ledger = pre.ledger;
     Real mpf[9], chz, chr;
     collide_f<Real, PR>(C, m, mf, chz_prev, chr_prev, chz, chr, mpf);
     const Node<Codec> own = V.out_node(loc);
