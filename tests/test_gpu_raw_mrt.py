@@ -94,3 +94,18 @@ def test_raw_reduced_precision_static_drop(prec, phi_tol):
     e = _errors(sim.fields(), run_oracle(case, 2000).fields())
     print(prec, "raw errors (max, L2):", e)
     assert e["phi"][0] < phi_tol[0] and e["phi"][1] < phi_tol[1], e
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mix_fp16"])
+def test_raw_launch_variants_bit_identical(prec):
+    """Every launch shape runs the raw-moment collision on the general-rate
+    kernels and computes the same numbers (walls and periodic z)."""
+    for case in (dict(W.with_raw_collision(W.static_drop(nr=45, nz=70, R=12.0)), precision=prec),
+                 dict(W.with_raw_collision(W.thread_breakup(nr=40, R0=12.0)), precision=prec)):
+        ref = None
+        for v in range(lbm.num_variants()):
+            f = run_gpu(case, 40, variant=v).fields()
+            if ref is None:
+                ref = f
+            for k in FIELDS:
+                assert np.array_equal(f[k], ref[k]), (prec, v, k)
