@@ -327,6 +327,9 @@ def run_cuda(args):
                 if other != prec:
                     line[f"batched_{other}"] = batched_other(torch, args, other, steps=min(args.steps, 50)
                                                              if other != "fp64" else 5)
+            for other in ("fp32", "mix_fp16"):
+                line[f"batched_{other}_raw_collision"] = batched_other(torch, args, other, min(args.steps, 50),
+                                                                      raw=True)
         line["single_case_fp32"] = single_case(torch, "oscillating", "fp32", min(args.steps, 50))
         line["single_case_fp64"] = single_case(torch, "oscillating", "fp64", min(max(4, args.steps // 4), 20))
     if rank == 0 and not args.no_cpu:
@@ -396,10 +399,13 @@ def e2e(cases, args, torch):
                             "read_back": "lbm_case_init_phase per case; lbm_case_diagnostics after every step"}}
 
 
-def batched_other(torch, args, prec, steps):
-    """The same batched case set in another precision (same timing method)."""
-    from paper_1810_09299_gb300 import lbm
+def batched_other(torch, args, prec, steps, raw=False):
+    """The same batched case set in another precision (same timing method);
+    raw: with the raw-moment collision option instead of the paper's."""
+    from paper_1810_09299_gb300 import lbm, workloads as W
     cases = build_cases("batched", prec, 0, args.cases)
+    if raw:
+        cases = [W.with_raw_collision(c) for c in cases]
     nodes = sum(c["nr"] * c["nz"] for c in cases)
     sim = lbm.Simulation(cases)
     for i, c in enumerate(cases):
@@ -412,7 +418,8 @@ def batched_other(torch, args, prec, steps):
     peak, kind = measured_peaks()
     ach = BYTES_PER_NODE[prec] * nodes / (ms * 1e-3) / 1e9
     sim.close()
-    out = {"precision": prec, "value": nodes / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
+    out = {"precision": prec, "collision": "raw moments" if raw else "orthogonal (paper)",
+           "value": nodes / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
            "variant": variant, "achieved_gbs": ach, "frac": ach / peak,
            "bytes_per_node": BYTES_PER_NODE[prec]}
     if prec == "fp64":

@@ -219,20 +219,22 @@ void fill_params(CaseReal<Real>& P, const lbm_params& p) {
     }
 }
 
-// The rate pattern of the paper's runs (Sec. 3.1): S^f = diag(1, 1, 1, s, s, s,
-// s, 1, 1) with one s; S^g = 1 except s1 = s7 = s8 derived from the local
-// viscosity.
-bool paper_rate_pattern(const lbm_params& p) {
-    if (p.collision != LBM_MRT_ORTHOGONAL) return false;
-    for (int i : {0, 1, 2, 7, 8})
-        if (p.sf[i] != 1.0) return false;
-    for (int i = 4; i <= 6; ++i)
-        if (p.sf[i] != p.sf[3]) return false;
+// The rate pattern of a case, when the kernels know it at compile time
+// (kRatesPaper / kRatesPaperRaw in lbm_internal.h), else kRatesGeneral.
+// Orthogonal moments, the paper's runs (Sec. 3.1): S^f = diag(1, 1, 1, s, s,
+// s, s, 1, 1) with one s; S^g = 1 except s1 = s7 = s8 derived from the local
+// viscosity.  Raw moments: S^f = 1 except one s on moments 1, 2, 6, 7; S^g = 1
+// except 3, 4, 5 derived from the local viscosity.
+int rate_pattern(const lbm_params& p) {
+    const bool raw = p.collision == LBM_MRT_RAW;
+    const int fs = raw ? 1 : 3;  // index of the f moment that carries s
     for (int i = 0; i < 9; ++i) {
-        const bool local = (i == 1 || i == 7 || i == 8);
-        if (local ? !(p.sg[i] < 0.0) : (p.sg[i] != 1.0)) return false;
+        const bool s_f = raw ? (i == 1 || i == 2 || i == 6 || i == 7) : (i >= 3 && i <= 6);
+        if (s_f ? (p.sf[i] != p.sf[fs]) : (p.sf[i] != 1.0)) return kRatesGeneral;
+        const bool local = raw ? (i >= 3 && i <= 5) : (i == 1 || i == 7 || i == 8);
+        if (local ? !(p.sg[i] < 0.0) : (p.sg[i] != 1.0)) return kRatesGeneral;
     }
-    return true;
+    return raw ? kRatesPaperRaw : kRatesPaper;
 }
 
 CaseDev make_case(const lbm_params& p, int64_t off) {
@@ -375,8 +377,10 @@ int create_impl(const lbm_params* cases, int32_t n, void* stream, lbm_handle** o
         h->max_nodes = std::max<int64_t>(h->max_nodes, (int64_t)cases[c].nz * cases[c].nr);
     }
     h->D.total = off;
-    h->D.paper_rates = true;
-    for (int c = 0; c < n; ++c) h->D.paper_rates = h->D.paper_rates && paper_rate_pattern(cases[c]);
+    // one rate mode for the whole handle: the pattern all cases share, else general
+    h->D.rate_mode = rate_pattern(cases[0]);
+    for (int c = 1; c < n; ++c)
+        if (rate_pattern(cases[c]) != h->D.rate_mode) h->D.rate_mode = kRatesGeneral;
     h->case_steps.assign(n, 0);
     h->initialized.assign(n, 0);
     int rc = LBM_OK;

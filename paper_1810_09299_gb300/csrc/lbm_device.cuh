@@ -647,10 +647,12 @@ __device__ __forceinline__ void inverse_moments_fg(const float* mf, const float*
 // Everything before the collisions for node (k, j) of case C, from the
 // shared phi window (centred on (a, b)) and the node's decoded g.
 //
-// PR ("paper rates"): the rate pattern of the paper's runs (Sec. 3.1) --
-// S^f = diag(1, 1, 1, s, s, s, s, 1, 1) and S^g = 1 except s1 = s7 = s8 =
-// 1/tau_g(x) -- is known at compile time, so unit-rate moments go straight to
-// their equilibrium and s_p = (s1 + s2 - s1 s2) / (2 s1 s2) = tau_g / 2.
+// RM (rate mode, lbm_internal.h): with kRatesPaper the rate pattern of the
+// paper's runs (Sec. 3.1) -- S^f = diag(1, 1, 1, s, s, s, s, 1, 1) and S^g = 1
+// except s1 = s7 = s8 = 1/tau_g(x) -- is known at compile time, so unit-rate
+// moments go straight to their equilibrium and s_p = (s1 + s2 - s1 s2) /
+// (2 s1 s2) = tau_g / 2; with kRatesPaperRaw the same choice in the raw basis
+// (s_3 = 1/tau_g, s_8 = 1) gives s_p = 3 tau_g / 2 - 1.
 //
 // inv_r_tab: when not null, 1 / r of the node's column (a table lookup
 // standing for the same correctly rounded quotient).
@@ -659,7 +661,7 @@ __device__ __forceinline__ void inverse_moments_fg(const float* mf, const float*
 // the 16-byte aligned FP32 block of the shared case record as two 16-byte
 // loads (measured -1.1 % on the mixed FP16 step, +0.2 % in FP32 storage, so
 // only the 16-bit codecs ask for it).
-template <typename Real, int LD, bool PR = false, bool VP = false>
+template <typename Real, int LD, int RM = kRatesGeneral, bool VP = false>
 __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, int a, int b, int j, const Real* mg,
                                             Real g0, Real p_prev, Macro<Real>& m, const Real* inv_r_tab = nullptr) {
     const CaseReal<Real>& P = case_params<Real>(C);
@@ -679,8 +681,10 @@ __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, 
     m.nu = m.phi * (VP ? (Real)v0.z : P.nu_l) + ((Real)1 - m.phi) * (VP ? (Real)v0.w : P.nu_g);  // Eq. 35
     const Real tau_g = (Real)3 * m.nu + (Real)0.5;                         // Eq. 34
     const Real sgv = rcp_(tau_g);
-    if constexpr (PR) {
+    if constexpr (RM == kRatesPaper) {
         m.sg[1] = sgv;
+    } else if constexpr (RM == kRatesPaperRaw) {
+        m.sg[3] = sgv;
     } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) m.sg[i] = ((C.sg_local >> i) & 1u) ? sgv : P.sg[i];
@@ -703,8 +707,10 @@ __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, 
     const Real drho = rho_l - rho_g;
     const Real dzrho = drho * m.gz, drrho = drho * m.gr;
     Real sp;
-    if constexpr (PR) {
+    if constexpr (RM == kRatesPaper) {
         sp = (Real)0.5 * tau_g;
+    } else if constexpr (RM == kRatesPaperRaw) {
+        sp = (Real)1.5 * tau_g - (Real)1;  // s_3 = 1/tau_g, s_8 = 1
     } else if (C.collision == 1) {
         // raw moments: Appendix C in that basis (x_0 = k_0 - k_3 + k_8)
         sp = (Real)1.5 * rcp_(m.sg[3]) - (Real)0.5 * rcp_(m.sg[8]) - (Real)0.5;
@@ -744,7 +750,7 @@ __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, 
 // ---------------------------------------------------------------- collisions
 // Phase field (Eq. 19 in moment space with Eq. 21-23).  chi = (r phi u_z,
 // r phi u_r + M phi); the time derivative of Eq. 38 uses chi^{n-1}.
-template <typename Real, bool PR = false>
+template <typename Real, int RM = kRatesGeneral>
 __device__ __forceinline__ void collide_f(const CaseDev& C, const Macro<Real>& m, const Real* mf, Real chi_z_prev,
                                           Real chi_r_prev, Real& chi_z, Real& chi_r, Real* mp) {
     const CaseReal<Real>& P = case_params<Real>(C);
@@ -755,9 +761,12 @@ __device__ __forceinline__ void collide_f(const CaseDev& C, const Macro<Real>& m
     const Real mR2 = (chi_r - chi_r_prev) + m.r * m.nrn * m.lam * (Real)(1.0 / 3.0);
     const Real meq[9] = {rphi, (Real)-2 * rphi, rphi, chi_z, -chi_z, chi_r, -chi_r, (Real)0, (Real)0};
     const Real mR[9] = {(Real)0, (Real)0, (Real)0, mR1, -mR1, mR2, -mR2, (Real)0, (Real)0};
-    if constexpr (PR) {
-        // unit rates: m0 is conserved, m1, m2, m7, m8 take their equilibria
-        const Real s = P.sf[3], h = (Real)1 - (Real)0.5 * s;
+    if constexpr (RM != kRatesGeneral) {
+        // unit rates: m0 is conserved, m1, m2, m7, m8 take their equilibria.
+        // The raw-moment pattern (rate s on c_z, c_r, c_z^2 c_r, c_z c_r^2)
+        // spans the same rate subspaces, so it is this very operator; its s
+        // is the rate of raw moment 1.
+        const Real s = RM == kRatesPaperRaw ? P.sf[1] : P.sf[3], h = (Real)1 - (Real)0.5 * s;
         mp[0] = rphi;
         mp[1] = meq[1];
         mp[2] = meq[2];
@@ -777,7 +786,7 @@ __device__ __forceinline__ void collide_f(const CaseDev& C, const Macro<Real>& m
 }
 
 // Hydrodynamics (Eq. 24 in moment space with Eq. 36-37).
-template <typename Real, bool PR = false>
+template <typename Real, int RM = kRatesGeneral>
 __device__ __forceinline__ void collide_g(const CaseDev& C, const Macro<Real>& m, Real* mp) {
     const CaseReal<Real>& P = case_params<Real>(C);
     const Real r = m.r, rho = m.rho, uz = m.uz, ur = m.ur, p = m.p;
@@ -799,13 +808,18 @@ __device__ __forceinline__ void collide_g(const CaseDev& C, const Macro<Real>& m
                         m.Fz, -m.Fz, m.Fr, -m.Fr,
                         (Real)(2.0 / 3.0) * (uz * dz_rr - ur * dr_rr),
                         (Real)(1.0 / 3.0) * (uz * dr_rr + ur * dz_rr)};
-    if constexpr (PR) {
+    if constexpr (RM == kRatesPaper) {
         const Real s = m.sg[1], h = (Real)1 - (Real)0.5 * s;
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             if (k == 1 || k == 7 || k == 8) mp[k] = m.mg[k] - s * (m.mg[k] - meq[k]) + h * MT[k];
             else mp[k] = meq[k] + (Real)0.5 * MT[k];
         }
+    } else if constexpr (RM == kRatesPaperRaw) {
+        // raw moments: the three second moments at 1/tau_g, the rest at 1
+        const Real s = m.sg[3];
+        const Real rates[9] = {(Real)1, (Real)1, (Real)1, s, s, s, (Real)1, (Real)1, (Real)1};
+        raw_relax<Real>(m.mg, meq, MT, rates, mp);
     } else if (C.collision == 1) {
         raw_relax<Real>(m.mg, meq, MT, m.sg, mp);
     } else {

@@ -17,6 +17,13 @@ constexpr int block_bytes_of(int f0_size, int pt_size, int real_size) {
     return (32 * f0_size + 17 * 32 * pt_size + 3 * 32 * real_size + 127) / 128 * 128;
 }
 
+// Rate modes of the step kernels: general rates read from the case record, or
+// a rate pattern every case of the handle shares and the kernels know at
+// compile time -- the paper's (Sec. 3.1: S^f = diag(1, 1, 1, s, s, s, s, 1, 1),
+// S^g = 1 except s_1 = s_7 = s_8 = 1/tau_g) or the same choice for the
+// raw-moment collision (f: s on raw moments 1, 2, 6, 7; g: 1/tau_g on 3, 4, 5).
+constexpr int kRatesGeneral = 0, kRatesPaper = 1, kRatesPaperRaw = 2;
+
 // Device buffers of a handle: two arrays of `total / 32` blocks (one block per
 // 32 nodes, see Block in lbm_device.cuh); index [parity] selects the buffer
 // read by the next step.
@@ -24,7 +31,7 @@ struct DeviceState {
     void* blk[2];
     void* cases;  // CaseDev[ncases] on the device
     int64_t total;
-    bool paper_rates;  // every case uses the rate pattern of the paper's runs (Sec. 3.1)
+    int rate_mode;     // kRatesGeneral, or the rate pattern every case shares (see below)
     const void* tmaps;  // CUtensorMap[ncases][2 tile heights][kMapsPerCase] in device memory
     int* status;        // device status word: nonzero after a bounded wait gave up
 };

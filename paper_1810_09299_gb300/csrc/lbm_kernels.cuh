@@ -50,10 +50,10 @@ __device__ __forceinline__ void ring_cell(int q, int& a, int& b) {
 // Minimum resident CTAs per SM requested from the register allocator: 32 warps
 // per SM (64 registers) for the FP32-arithmetic kernels with the paper's rate
 // pattern, which fit without spilling; 24 warps for general rates.
-template <class Codec, int BZ, bool PR>
+template <class Codec, int BZ, int RM>
 constexpr int step_min_blocks() {
     return sizeof(typename Codec::Real) == 8 ? 1
-           : PR ? (BZ >= 16 ? 2 : (BZ >= 8 ? 4 : 8))
+           : RM != kRatesGeneral ? (BZ >= 16 ? 2 : (BZ >= 8 ? 4 : 8))
                 : (BZ >= 16 ? 1 : (BZ >= 8 ? 3 : 6));
 }
 
@@ -140,7 +140,7 @@ __device__ __forceinline__ void node_pre(const typename Codec::F0T& f0raw, const
 // invr: when not null, 1 / r of window column b - 1, b, b + 1 at invr[b - 1 ..
 // b + 1] (the same quotients the node would compute itself).  fdec: see
 // node_pre.
-template <class Codec, bool PR, int LD>
+template <class Codec, int RM, int LD>
 __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Codec>& V, const typename Codec::Real* sphi,
                                             int a, int b, int k, int j, int loc,
                                             const typename Codec::F0T& f0raw, const typename Codec::PT* fraw,
@@ -154,17 +154,17 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     node_pre<Codec>(f0raw, fraw, graw, r, pre, fdec);
     const Real* mf = pre.mf;
     Macro<Real> m;
-    node_macros<Real, LD, PR, sizeof(typename Codec::PT) == 2>(C, sphi, a, b, j, pre.mg, pre.g0, p_prev, m,
+    node_macros<Real, LD, RM, sizeof(typename Codec::PT) == 2>(C, sphi, a, b, j, pre.mg, pre.g0, p_prev, m,
                                                                invr ? invr + b : nullptr);
     FF2 ledger = pre.ledger;
     Real mpf[9], chz, chr;
-    collide_f<Real, PR>(C, m, mf, chz_prev, chr_prev, chz, chr, mpf);
+    collide_f<Real, RM>(C, m, mf, chz_prev, chr_prev, chz, chr, mpf);
     const Node<Codec> own = V.out_node(loc);
     own.chz() = chz;
     own.chr() = chr;
     if (C.p_coupling == 1) own.p() = m.p;
     Real mpg[9];
-    collide_g<Real, PR>(C, m, mpg);
+    collide_g<Real, RM>(C, m, mpg);
     Real fp[9], gp[9];
     inverse_moments_fg(mpf, mpg, fp, gp);
     // 5. streaming (Eq. 20).  Rows j-1, j, j+1 are the only destinations, so
@@ -254,8 +254,8 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
 // the loads of its own node; the node's phi goes to the shared window straight
 // from those registers and only the two-node ring around the tile is
 // recomputed from neighbours' populations.
-template <class Codec, int BZ, bool PR>
-__global__ void __launch_bounds__(kTR * BZ, (step_min_blocks<Codec, BZ, PR>()))
+template <class Codec, int BZ, int RM>
+__global__ void __launch_bounds__(kTR * BZ, (step_min_blocks<Codec, BZ, RM>()))
 step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles, StateDev<Codec> S,
             const CUtensorMap* __restrict__ maps, int map_set, int parity, int ntiles, int ahead) {
     using Real = typename Codec::Real;
@@ -352,7 +352,7 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     __syncthreads();
     if (!inside) return;
 
-    node_update<Codec, PR, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw, graw, chz_prev,
+    node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw, graw, chz_prev,
                                chr_prev, p_prev, kInvrTable ? s_invr : nullptr, kKeepF ? f : nullptr);
 }
 
@@ -443,7 +443,7 @@ constexpr int pipe_min_blocks() {
 // number of tries.  A timeout sets the status word; the timed-out stage gets a
 // second bounded wait and the CTA leaves.  Nothing else of its own is in
 // flight then, since the next stage is issued only after a successful wait.
-template <class Codec, int BZ, bool PR>
+template <class Codec, int BZ, int RM>
 __global__ void __launch_bounds__(kTR * BZ, (pipe_min_blocks<Codec, BZ>()))
 step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles, int ntiles,
                  StateDev<Codec> S, const CUtensorMap* __restrict__ maps, int map_set, int parity,
@@ -538,7 +538,7 @@ step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
         __syncthreads();
         if (inside) {
             const int loc = k * C.pitch + j;
-            node_update<Codec, PR, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw, graw,
+            node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw, graw,
                                        chz_prev, chr_prev, p_prev, nullptr, sizeof(PT) == 2 ? f : nullptr);
         }
         if (NS == 1) {
@@ -724,25 +724,25 @@ StateDev<Codec> make_state(const DeviceState& D, int parity) {
 
 // Persistent grid for the pipelined kernel: as many CTAs as fit on the GPU at
 // once (queried per instantiation), capped by the tile count.
-template <class Codec, int BZ, bool PR>
+template <class Codec, int BZ, int RM>
 void launch_tma(int ntiles, cudaStream_t st, const CaseDev* cs, const TileDev* tiles, const StateDev<Codec>& S,
                 const DeviceState& D, int parity) {
     using L = TmaTile<Codec, BZ>;
     static int grid_cap = 0;
     if (grid_cap == 0) {
-        cudaFuncSetAttribute(step_kernel_pipe<Codec, BZ, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+        cudaFuncSetAttribute(step_kernel_pipe<Codec, BZ, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel_pipe<Codec, BZ, PR>, kTR * BZ, L::bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel_pipe<Codec, BZ, RM>, kTR * BZ, L::bytes);
         grid_cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
     }
     const int grid = ntiles < grid_cap ? ntiles : grid_cap;
-    step_kernel_pipe<Codec, BZ, PR><<<grid, dim3(kTR, BZ), L::bytes, st>>>(
+    step_kernel_pipe<Codec, BZ, RM><<<grid, dim3(kTR, BZ), L::bytes, st>>>(
         cs, tiles, ntiles, S, (const CUtensorMap*)D.tmaps, BZ == 8 ? 0 : 1, parity, D.status);
 }
 
-template <class Codec, bool PR>
+template <class Codec, int RM>
 void launch_step_rates(int variant, int ntiles, cudaStream_t st, const CaseDev* cs, const TileDev* tiles,
                        const StateDev<Codec>& S, const DeviceState& D, int parity) {
     // prefetch distance: the CTAs resident at once (SMs x CTAs per SM)
@@ -756,19 +756,19 @@ void launch_step_rates(int variant, int ntiles, cudaStream_t st, const CaseDev* 
     const CUtensorMap* maps = (const CUtensorMap*)D.tmaps;
     switch (variant) {
         case 0:
-            step_kernel<Codec, 8, PR><<<ntiles, dim3(kTR, 8), 0, st>>>(
-                cs, tiles, S, maps, 0, parity, ntiles, kPrefetchQuarters * sms * step_min_blocks<Codec, 8, PR>() / 4);
+            step_kernel<Codec, 8, RM><<<ntiles, dim3(kTR, 8), 0, st>>>(
+                cs, tiles, S, maps, 0, parity, ntiles, kPrefetchQuarters * sms * step_min_blocks<Codec, 8, RM>() / 4);
             break;
         case 1:
-            step_kernel<Codec, 16, PR><<<ntiles, dim3(kTR, 16), 0, st>>>(
-                cs, tiles, S, maps, 1, parity, ntiles, kPrefetchQuarters * sms * step_min_blocks<Codec, 16, PR>() / 4);
+            step_kernel<Codec, 16, RM><<<ntiles, dim3(kTR, 16), 0, st>>>(
+                cs, tiles, S, maps, 1, parity, ntiles, kPrefetchQuarters * sms * step_min_blocks<Codec, 16, RM>() / 4);
             break;
         case 2:
-            step_kernel<Codec, 4, PR><<<ntiles, dim3(kTR, 4), 0, st>>>(
-                cs, tiles, S, maps, 0, parity, ntiles, kPrefetchQuarters * sms * step_min_blocks<Codec, 4, PR>() / 4);
+            step_kernel<Codec, 4, RM><<<ntiles, dim3(kTR, 4), 0, st>>>(
+                cs, tiles, S, maps, 0, parity, ntiles, kPrefetchQuarters * sms * step_min_blocks<Codec, 4, RM>() / 4);
             break;
-        case 3: launch_tma<Codec, 8, PR>(ntiles, st, cs, tiles, S, D, parity); break;
-        default: launch_tma<Codec, 16, PR>(ntiles, st, cs, tiles, S, D, parity); break;
+        case 3: launch_tma<Codec, 8, RM>(ntiles, st, cs, tiles, S, D, parity); break;
+        default: launch_tma<Codec, 16, RM>(ntiles, st, cs, tiles, S, D, parity); break;
     }
 }
 
@@ -778,8 +778,10 @@ cudaError_t launch_step_t(const DeviceState& D, int parity, int variant, const T
     if (ntiles <= 0) return cudaSuccess;
     StateDev<Codec> S = make_state<Codec>(D, parity);
     const CaseDev* cs = (const CaseDev*)D.cases;
-    if (D.paper_rates) launch_step_rates<Codec, true>(variant, ntiles, st, cs, tiles, S, D, parity);
-    else launch_step_rates<Codec, false>(variant, ntiles, st, cs, tiles, S, D, parity);
+    if (D.rate_mode == kRatesPaper) launch_step_rates<Codec, kRatesPaper>(variant, ntiles, st, cs, tiles, S, D, parity);
+    else if (D.rate_mode == kRatesPaperRaw)
+        launch_step_rates<Codec, kRatesPaperRaw>(variant, ntiles, st, cs, tiles, S, D, parity);
+    else launch_step_rates<Codec, kRatesGeneral>(variant, ntiles, st, cs, tiles, S, D, parity);
     return cudaGetLastError();
 }
 
