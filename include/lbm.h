@@ -76,7 +76,9 @@ typedef enum { LBM_P_EXACT = 0, LBM_P_LAGGED = 1 } lbm_p_coupling;
  *                       redone in this basis).  The paper's rate choice reads
  *                       sf = (1, s, s, 1, 1, 1, s, s, 1), for which the f-collision
  *                       is the paper's own, and sg = 1 except s_3 = s_4 = s_5 =
- *                       1/tau_g.  Cases with this basis run the general-rate
+ *                       1/tau_g.  With this choice (rates derived as in the
+ *                       paper) the step runs kernels specialised for it, as for
+ *                       the paper's own pattern; other rates run the general
  *                       kernels. */
 typedef enum { LBM_MRT_ORTHOGONAL = 0, LBM_MRT_RAW = 1 } lbm_collision;
 
