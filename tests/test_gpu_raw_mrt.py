@@ -1,5 +1,7 @@
 """The raw-moment (non-orthogonal) MRT option through the C ABI against the
-FP64 oracle's raw-moment option (needs a GB300).
+FP64 oracle's raw-moment option (needs a GB300).  Cases with the paper's rate
+choice in the raw basis run the kernels specialised for it; SF_ANY / SG_ANY
+and the mixed-basis batch run the general-rate kernels.
 
 The CUDA path keeps the orthogonal moments it already forms and maps their
 deviations into the raw basis and back with fixed combinations; the oracle
@@ -98,8 +100,8 @@ def test_raw_reduced_precision_static_drop(prec, phi_tol):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "mix_fp16"])
 def test_raw_launch_variants_bit_identical(prec):
-    """Every launch shape runs the raw-moment collision on the general-rate
-    kernels and computes the same numbers (walls and periodic z)."""
+    """Every launch shape computes the same numbers with the raw-moment
+    collision (its compile-time rate mode; walls and periodic z)."""
     for case in (dict(W.with_raw_collision(W.static_drop(nr=45, nz=70, R=12.0)), precision=prec),
                  dict(W.with_raw_collision(W.thread_breakup(nr=40, R0=12.0)), precision=prec)):
         ref = None
