@@ -45,10 +45,11 @@ BYTES_PER_NODE = {
 DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf16": "f32 (bf16 storage)"}
 # DRAM bytes per node update of the step kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the nodes of the captured
-# launch; profiles/step_kernel_fp32_batched64cases.md), keyed by precision and
-# launch variant.  Scaled to a full launch by the node count.  Kept only for
+# launch; profiles/step_kernel_fp32_batched64cases.md), keyed by precision,
+# launch variant and collision basis.  Scaled to a full launch by the node count.  Kept only for
 # the kernel build that was captured.
-TRAFFIC_B_PER_NODE = {("fp32", 0): 164.86}
+TRAFFIC_B_PER_NODE = {("fp32", 0, "orthogonal"): 164.86,
+                      ("fp32", 0, "raw"): 164.92}  # profiles/step_kernel_fp32_raw_batched64cases.md
 # The FP64 step is bound by the FP64 pipe, not by HBM: FP64-pipe thread
 # instructions (DADD + DFMA + DMUL) per node update from one ncu capture
 # (profiles/step_kernel_fp64_batched64cases.md), against the pipe's peak of
@@ -250,6 +251,9 @@ def run_cuda(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     prec = args.precision
     cases = build_cases(args.workload, prec, rank, args.cases)
+    if args.collision == "raw":
+        from paper_1810_09299_gb300 import workloads as W
+        cases = [W.with_raw_collision(c) for c in cases]
     nodes = sum(c["nr"] * c["nz"] for c in cases)
     sim = lbm.Simulation(cases)
     for i, c in enumerate(cases):
@@ -298,13 +302,14 @@ def run_cuda(args):
                                 "oscillating": "oscillating P2 drop, 128x256, R0=32",
                                 "static": "static drop, 64x128, R=16"}[args.workload],
                    "precision": prec, "nodes_per_gpu": nodes, "cases_per_gpu": len(cases),
+                   "collision": "raw moments" if args.collision == "raw" else "orthogonal (paper)",
                    "l2": "flushed between timed steps" if flush_buf is not None else
                          "inputs larger than L2 (no flush)",
                    "variant": variant, "parallelism": f"independent cases per GPU x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": (TRAFFIC_B_PER_NODE[(prec, variant)] * nodes
-                                 if (prec, variant) in TRAFFIC_B_PER_NODE else None),
+                     "traffic": (TRAFFIC_B_PER_NODE[(prec, variant, args.collision)] * nodes
+                                 if (prec, variant, args.collision) in TRAFFIC_B_PER_NODE else None),
                      "traffic_unit": "bytes per launch (ncu capture of 64 cases scaled by node count)",
                      "note": f"peak {peak_kind}; algorithmic bytes {BYTES_PER_NODE[prec]} B/node x {nodes} nodes "
                              f"per launch / mean CUDA-event launch duration"},
@@ -460,6 +465,8 @@ def main():
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--workload", default="batched", choices=["batched", "oscillating", "static"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "mix_fp16", "mix_bf16"])
+    ap.add_argument("--collision", default="orthogonal", choices=["orthogonal", "raw"],
+                    help="moment basis of both collisions (raw: the raw-moment option)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
