@@ -48,8 +48,7 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf
 # launch; profiles/step_kernel_fp32_batched64cases.md), keyed by precision,
 # launch variant and collision basis.  Scaled to a full launch by the node count.  Kept only for
 # the kernel build that was captured.
-TRAFFIC_B_PER_NODE = {("fp32", 0, "orthogonal"): 164.86,
-                      ("fp32", 0, "raw"): 164.92}  # profiles/step_kernel_fp32_raw_batched64cases.md
+TRAFFIC_B_PER_NODE = {("fp32", 0, "orthogonal"): 164.96}
 # The FP64 step is bound by the FP64 pipe, not by HBM: FP64-pipe thread
 # instructions (DADD + DFMA + DMUL) per node update from one ncu capture
 # (profiles/step_kernel_fp64_batched64cases.md), against the pipe's peak of

@@ -47,13 +47,19 @@ __device__ __forceinline__ void ring_cell(int q, int& a, int& b) {
     }
 }
 
-// Minimum resident CTAs per SM requested from the register allocator: 32 warps
-// per SM (64 registers) for the FP32-arithmetic kernels with the paper's rate
-// pattern, which fit without spilling; 24 warps for general rates.
+// Minimum resident CTAs per SM requested from the register allocator.  The
+// FP32-arithmetic kernels with a compile-time rate pattern take 5 CTAs of 8
+// rows (40 warps per SM, 48 registers a thread, a few bytes of spill): against
+// 4 CTAs (64 registers, no spill) that measured -3.4 % in FP32, -2.2 % in
+// FP16 and -5.1 % in BF16 storage with the paper's collision, with the same
+// results.  The raw-moment collision in 16-bit storage spills more at 48
+// registers and keeps 4 CTAs (0.772 against 0.817 ms).  General rates: 24
+// warps.
 template <class Codec, int BZ, int RM>
 constexpr int step_min_blocks() {
+    constexpr int bz8 = (RM == kRatesPaperRaw && sizeof(typename Codec::PT) == 2) ? 4 : 5;
     return sizeof(typename Codec::Real) == 8 ? 1
-           : RM != kRatesGeneral ? (BZ >= 16 ? 2 : (BZ >= 8 ? 4 : 8))
+           : RM != kRatesGeneral ? (BZ >= 16 ? 2 : (BZ >= 8 ? bz8 : 8))
                 : (BZ >= 16 ? 1 : (BZ >= 8 ? 3 : 6));
 }
 
