@@ -41,6 +41,28 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(lbm.LbmDiag) == 11 * 8
 
 
+def _header_struct_fields(name):
+    """Field names of `typedef struct { ... } name;` in include/lbm.h, in order."""
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", src).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(","):
+            tok = part.strip().split()[-1]
+            names.append(re.sub(r"\[.*\]", "", tok))
+    return names
+
+
+def test_binding_fields_follow_the_header():
+    """The ctypes mirrors of lbm_params and lbm_diag name the header's fields in its order."""
+    assert [f[0] for f in lbm.LbmParams._fields_] == _header_struct_fields("lbm_params")
+    assert [f[0] for f in lbm.LbmDiag._fields_] == _header_struct_fields("lbm_diag")
+
+
 def test_strerror_and_static_queries(L):
     assert lbm.strerror(0) == "ok"
     assert "invalid" in lbm.strerror(lbm.LBM_ERR_INVALID_ARG)
