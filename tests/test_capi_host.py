@@ -95,3 +95,21 @@ def test_invalid_arguments_rejected_before_device_work(L):
     arr = (lbm.LbmParams * 2)(lbm.make_params(dict(workloads.static_drop(nr=16, nz=16, R=4.0), precision="fp32")),
                               lbm.make_params(workloads.static_drop(nr=16, nz=16, R=4.0)))
     assert L.lbm_batch_create(arr, 2, None, ctypes.byref(h)) == lbm.LBM_ERR_INVALID_ARG
+
+
+def test_oracle_binding_fields_follow_its_header():
+    """The same check for the oracle's parameter and diagnostics blocks."""
+    import oracle
+
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "oracle", "axilbm_oracle.h")).read(), flags=re.S)
+
+    def fields(name):
+        body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", src).group(1)
+        out = []
+        for decl in filter(None, (d.strip() for d in body.split(";"))):
+            for part in decl.split(","):
+                out.append(re.sub(r"\[.*\]", "", part.strip().split()[-1]))
+        return out
+
+    assert [f[0] for f in oracle.OrcParams._fields_] == fields("orc_params")
+    assert [f[0] for f in oracle.OrcDiag._fields_] == fields("orc_diag")
