@@ -43,9 +43,8 @@ def test_struct_layouts_match_header():
 
 def _header_struct_fields(name):
     """Field names of `typedef struct { ... } name;` in include/lbm.h, in order."""
-    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "lbm.h")).read(), flags=re.S)
     body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", src).group(1)
-    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     names = []
     for decl in body.split(";"):
         decl = decl.strip()
