@@ -638,7 +638,10 @@ int orc_set_aux(orc_state* s, const double* chi_z, const double* chi_r, const do
 
 int64_t orc_step_count(const orc_state* s) { return s->steps; }
 
-/* Diagnostics: plain FP64 sums in node order. */
+/* Diagnostics: plain FP64 sums in node order.  A node whose phi, u_z, u_r or
+ * p is not finite is counted in `nonfinite` and left out of every sum and
+ * extremum (the paper defines these quantities for finite states only; the
+ * count says how many nodes were left out). */
 int orc_diagnostics(orc_state* s, orc_diag* out)
 {
     const int nr = s->prm.nr, nz = s->prm.nz;
@@ -659,7 +662,10 @@ int orc_diagnostics(orc_state* s, orc_diag* out)
         for (int j = 0; j < nr; ++j) {
             size_t n = (size_t)k * nr + j;
             double r = radius(j), z = k + 0.5;
-            if (!isfinite(ph[n]) || !isfinite(uz[n]) || !isfinite(ur[n]) || !isfinite(p[n])) bad += 1;
+            if (!isfinite(ph[n]) || !isfinite(uz[n]) || !isfinite(ur[n]) || !isfinite(p[n])) {
+                bad += 1;
+                continue;
+            }
             mass += r * ph[n];
             double uu = uz[n] * uz[n] + ur[n] * ur[n];
             ke += 0.5 * r * rh[n] * uu;

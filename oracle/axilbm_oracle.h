@@ -49,7 +49,8 @@ typedef struct {
 
 typedef struct orc_state orc_state;
 
-/* Diagnostics record (all FP64). */
+/* Diagnostics record (all FP64).  Nodes whose phi, u_z, u_r or p is not
+ * finite are left out of every sum and extremum and counted in nonfinite. */
 typedef struct {
     double step;            /* number of completed time steps */
     double mass;            /* sum_nodes r*phi (= sum of all f) */
@@ -60,7 +61,7 @@ typedef struct {
     double phi_min, phi_max;
     double axis_half_length;   /* half the length of phi>1/2 along the axis row j=0 */
     double radial_half_length; /* phi=1/2 crossing along r on the row nearest z_centroid */
-    double nonfinite;       /* count of non-finite phi, u or p values */
+    double nonfinite;       /* number of nodes with a non-finite phi, u or p */
 } orc_diag;
 
 orc_state* orc_create(const orc_params* prm);

@@ -270,3 +270,22 @@ def test_mixed_precision_static_drop(prec, phi_tol):
         R_eff = (3 * 2 * math.pi * np.sum(r * got["phi"]) / (4 * math.pi)) ** (1 / 3)
         lap = 2 * case["sigma"] / R_eff
         assert abs(d["dp"] - lap) / lap < 0.01, (d["dp"], lap)
+
+
+def test_diagnostics_leave_out_nonfinite_nodes_like_the_oracle():
+    """One NaN in phi0 reaches u and p of its 16 stencil neighbours (Eq. 39-40).
+    The GPU record and the oracle record both count those 17 nodes and leave
+    them out of every sum and extremum, so the two records agree."""
+    case = W.static_drop(nr=40, nz=72, R=12.0)
+    phi = W.initial_phi(case)
+    phi[30, 20] = np.nan
+    sim = lbm.Simulation(case)
+    sim.init_phase(0, "host_array", phi=phi)
+    dg = sim.diagnostics(check=False)
+    do = oracle.Oracle(case).init(phi).diagnostics()
+    assert dg["status"] == lbm.LBM_ERR_NONFINITE
+    assert dg["nonfinite"] == do["nonfinite"] == 17
+    for k in ("mass", "kinetic", "z_centroid", "dp", "umax", "phi_min", "phi_max", "axis_half_length",
+              "radial_half_length"):
+        assert math.isfinite(dg[k]), k
+        assert abs(dg[k] - do[k]) <= 1e-12 * max(abs(do[k]), 1e-12), (k, dg[k], do[k])
