@@ -41,7 +41,7 @@ typedef enum {
     LBM_ERR_INVALID_ARG = -1,  /* a parameter is out of range or a pointer is NULL */
     LBM_ERR_CUDA = -2,         /* a CUDA runtime call or a kernel launch failed */
     LBM_ERR_NONFINITE = -3,    /* a NaN or Inf appeared in phi, u or p */
-    LBM_ERR_TIMEOUT = -4,      /* a bounded device wait gave up */
+    LBM_ERR_TIMEOUT = -4,      /* a bounded device wait gave up (see lbm_step) */
     LBM_ERR_OOM = -5,          /* device allocation failed */
     LBM_ERR_STATE = -6         /* call out of order (e.g. lbm_step before lbm_init_phase) */
 } lbm_status;
@@ -109,8 +109,15 @@ typedef struct {
     double n_eps;
 } lbm_params;
 
-/* Diagnostics record, all FP64, computed on the device with compensated
- * (Neumaier) sums in a fixed order (deterministic).
+/* Diagnostics record: the quantities the paper reads off its runs -- the
+ * conserved sum of r phi (Eq. 16), the pressure jump of Laplace's law and the
+ * spurious-velocity maximum of the static drop (Sec. 3.1), the axis half-length
+ * whose oscillation gives the frequency of Sec. 3.2 (Eq. 43-45) -- all FP64,
+ * computed on the device in a fixed order (deterministic): each of a fixed set
+ * of blocks sums its nodes plainly and then pairwise, and the block results
+ * are combined with compensated (Neumaier) sums.  A node whose phi, u_z, u_r
+ * or p is not finite is left out of every sum and extremum and counted in
+ * nonfinite.
  *   mass               sum over nodes of r phi (equal to the sum of all f_i).
  *   kinetic            sum of 0.5 r rho |u|^2.
  *   z_centroid         sum r z phi / sum r phi.
@@ -146,6 +153,10 @@ enum { LBM_FIELD_PHI = 1, LBM_FIELD_RHO = 2, LBM_FIELD_UZ = 4, LBM_FIELD_UR = 8,
  * with pitch = nr rounded up to 32), allocates the device state (LBM_ERR_OOM)
  * and selects the current CUDA device.  *out is set on success. */
 int lbm_create(const lbm_params* prm, void* stream, lbm_handle** out);
+/* The parameters are those of the paper's model: the densities of Eq. 17,
+ * the viscosities of Eq. 35 that give tau_g through Eq. 34, sigma and W that
+ * give beta and k of Eq. 4, the mobility that gives tau_f through Eq. 18, and
+ * the diagonal rates of Eq. 13 (phase field) and Eq. 28 (hydrodynamics). */
 
 /* Create a batch of ncases independent cases (ncases >= 1) that advance together:
  * each lbm_step launch covers the tiles of every case (Sec. 3's test problems run
@@ -180,18 +191,25 @@ int lbm_init_phase_all(lbm_handle* h, const double* host_phi);
  * (hydrodynamic collision) -> Eq. 20 (streaming with axis reflection and
  * bounce-back).  Asynchronous on the handle's stream; repeated steps are
  * replayed from a captured CUDA graph.  Returns launch errors immediately and
- * earlier sticky errors. */
+ * earlier sticky errors.  The launch shapes that stage tiles through shared
+ * memory with TMA copies (lbm_set_variant) wait on them with a bounded number
+ * of polls; a wait that gives up is reported later as LBM_ERR_TIMEOUT.  A copy
+ * of that CTA may then still have been in flight when it left, so after
+ * LBM_ERR_TIMEOUT treat the CUDA context as suspect: destroy the handle and
+ * create a new one (in a new process if the error returns). */
 int lbm_step(lbm_handle* h, int64_t nsteps);
 
 /* Copy macroscopic fields of case 0 / case icase to the host:
  * host_out holds popcount(mask) arrays of [nz][nr] doubles, in bit order of
- * LBM_FIELD_*.  u and p are recomputed from the current populations exactly as
- * the next step would compute them.  Synchronises. */
+ * LBM_FIELD_*: phi = sum f_i / r (Eq. 16), rho (Eq. 17), u (Eq. 31-32) and
+ * p (Eq. 33, solved with u_r as lbm_p_coupling says), recomputed from the
+ * current populations exactly as the next step computes them.  Synchronises. */
 int lbm_get_fields(lbm_handle* h, int32_t mask, double* host_out);
 int lbm_case_get_fields(lbm_handle* h, int32_t icase, int32_t mask, double* host_out);
 
-/* Diagnostics of case 0 / case icase (see lbm_diag).  Synchronises.  Returns
- * LBM_ERR_NONFINITE (and fills *out) if any phi, u or p is not finite. */
+/* Diagnostics of case 0 / case icase (see lbm_diag: the quantities of
+ * Sec. 3.1-3.2).  Synchronises.  Returns LBM_ERR_NONFINITE (and fills *out)
+ * if any phi, u or p is not finite. */
 int lbm_diagnostics(lbm_handle* h, lbm_diag* out);
 int lbm_case_diagnostics(lbm_handle* h, int32_t icase, lbm_diag* out);
 
@@ -264,7 +282,10 @@ int64_t lbm_kernel_launches(const lbm_handle* h);
  * exits.  Requires nz, nr >= 1 and nz * nr <= 2^31 - 1, else
  * LBM_ERR_INVALID_ARG.  The first call on a device looks up that array's
  * device address on the current device; make that first call before any stream
- * capture.  All calls share the array (its contents are fully rewritten by
+ * capture.  The address is kept for the life of the process: after
+ * cudaDeviceReset (or anything else that replaces the device's primary
+ * context) it is stale, so do not call this entry point again in that
+ * process.  All calls share the array (its contents are fully rewritten by
  * each call), so calls that overlap on the GPU, e.g. on two streams, race. */
 int lbm_diag_reduce_noalloc(const double* d_fields, int32_t nz, int32_t nr, int32_t z_periodic, double step,
                             double* d_out, void* stream);
@@ -278,7 +299,8 @@ int lbm_diag_reduce_noalloc(const double* d_fields, int32_t nz, int32_t nr, int3
  * `stream`.  The context stays usable: the kernel leaves no work in flight. */
 int lbm_selftest_bounded_wait(int32_t tries, void* stream, int32_t* device_status_word);
 
-/* Release every resource of the handle (NULL is ignored). */
+/* Release every resource of the handle (NULL is ignored).  No paper
+ * counterpart: resource management only. */
 int lbm_destroy(lbm_handle* h);
 
 /* Static description of a status code. */

@@ -1,0 +1,124 @@
+"""Evidence for three readings of the paper, taken on the FP64 oracle.
+
+* Stability window of the viscosity.  With the paper's rates (Sec. 3.1:
+  S^g = 1 except s_1 = s_7 = s_8 = 1/tau_g, Eq. 34) a liquid at rest loses
+  its rest state for nu = 0.05 and nu = 0.25 but keeps it for nu = 0.1 (the
+  paper's own value in every run of Sec. 3), with either reading of the
+  pressure coupling of Eq. 32-33.  A viscosity ratio of 10 at a density ratio
+  of 100 therefore needs a viscosity outside the window, and such a drop
+  turns non-finite within a hundred steps.
+* Mobility of the rising bubble.  The bubble with M = 0.02 turns non-finite,
+  the same bubble with M = 0.05 does not (reduced grid).
+* Horizon of the FP64 parity checks.  Two FP64 runs whose initial phi
+  differ by 1e-15 stay within round-off of each other for a few hundred
+  steps on the moving P2 drop and then separate (the interface normal of
+  Eq. 2 turns on round-off where phi overshoots 1 in the moving liquid); on
+  grids that the drop fills, and with the raw-moment collision, they
+  separate within tens of steps; on the static drop they stay together.
+  The CUDA-vs-oracle parity tests compare inside these horizons.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_09299_gb300 import workloads as W
+
+
+def _uniform_liquid(nu, p_coupling, nr=16, nz=32):
+    c = W.base_case(nr=nr, nz=nz, z_periodic=1, rho_l=1.0, rho_g=0.01, nu_l=nu, nu_g=nu, sigma=0.005,
+                    W=4.0, mobility=0.05, p_coupling=p_coupling)
+    o = oracle.Oracle(c).init(np.ones((nz, nr)))
+    f, g = o.populations()
+    g = g + 1e-8 * np.random.default_rng(1).standard_normal(g.shape)
+    o.set_populations(f, g)
+    return o
+
+
+def _speed(o):
+    F = o.fields()
+    return float(np.max(np.hypot(F["uz"], F["ur"])))
+
+
+@pytest.mark.parametrize("p_coupling", [0, 1])
+@pytest.mark.parametrize("nu", [0.05, 0.25])
+def test_rest_state_is_lost_outside_the_viscosity_window(nu, p_coupling):
+    o = _uniform_liquid(nu, p_coupling)
+    o.step(1000)
+    s = _speed(o)
+    assert not (s < 1e-3), s  # grown by five orders of magnitude, or no longer finite
+
+
+@pytest.mark.parametrize("p_coupling", [0, 1])
+def test_rest_state_is_kept_inside_the_viscosity_window(p_coupling):
+    o = _uniform_liquid(0.1, p_coupling)
+    o.step(3000)
+    assert _speed(o) < 1e-4
+
+
+@pytest.mark.parametrize("nu_l,nu_g", [(0.05, 0.5), (0.5, 0.05)])
+def test_viscosity_ratio_10_at_density_ratio_100_diverges(nu_l, nu_g):
+    """The oscillating drop of the benchmark's second configuration (density
+    ratio 100) with a viscosity ratio of 10, on a reduced grid."""
+    case = W.oscillating_drop(nr=48, nz=90, R0=16.0, nu_l=nu_l, nu_g=nu_g)
+    o = oracle.Oracle(case).init(W.initial_phi(case)).step(300)
+    assert o.diagnostics()["nonfinite"] > 0
+    ref = W.oscillating_drop(nr=48, nz=90, R0=16.0)
+    o = oracle.Oracle(ref).init(W.initial_phi(ref)).step(1000)
+    assert o.diagnostics()["nonfinite"] == 0
+
+
+def test_bubble_mobility_002_diverges_005_does_not():
+    """Rising bubble (density ratio 1000, W = 5, Eo = 10 with nu_l = 0.08) on
+    a 32 x 128 grid, R = 8."""
+    small = dict(nr=32, nz=128, R=8.0, zc=32.0, precision="fp64")
+    bad = W.rising_bubble(mobility=0.02, **small)
+    o = oracle.Oracle(bad).init(W.initial_phi(bad)).step(1000)
+    assert o.diagnostics()["nonfinite"] > 0
+    good = W.rising_bubble(mobility=0.05, **small)
+    o = oracle.Oracle(good).init(W.initial_phi(good)).step(3000)
+    d = o.diagnostics()
+    assert d["nonfinite"] == 0 and d["umax"] < 0.1
+
+
+def _separation(case, checkpoints):
+    """Relative max-norm difference of phi between two runs whose phi0 differ
+    by at most 1e-15, at each checkpoint."""
+    phi0 = W.initial_phi(case)
+    phi1 = phi0 + 1e-15 * np.random.default_rng(7).uniform(-1.0, 1.0, phi0.shape)
+    a = oracle.Oracle(case).init(phi0)
+    b = oracle.Oracle(case).init(phi1)
+    out, last = [], 0
+    for n in checkpoints:
+        a.step(n - last)
+        b.step(n - last)
+        last = n
+        pa, pb = a.fields()["phi"], b.fields()["phi"]
+        out.append(float(np.max(np.abs(pa - pb)) / np.max(np.abs(pa))))
+    return out
+
+
+def test_horizon_moving_p2_drop():
+    """128 x 256 P2 drop: parity is compared at 250 steps."""
+    e250, e500 = _separation(W.oscillating_drop(), [250, 500])
+    assert e250 < 1e-11 and e500 > 1e-8, (e250, e500)
+
+
+@pytest.mark.parametrize("nr,nz,zper", [(33, 5, 1), (5, 41, 0)])
+def test_horizon_filled_grids(nr, nz, zper):
+    """Grids the drop fills: parity is compared at 10 steps."""
+    case = W.static_drop(nr=nr, nz=nz, R=max(nr, nz) / 2.0, z_periodic=zper)
+    e10, e30 = _separation(case, [10, 30])
+    assert e10 < 1e-13 and e30 > 1e-10, (e10, e30)
+
+
+def test_horizon_raw_moment_p2_drop():
+    """Raw-moment collision on the 128 x 256 P2 drop: parity is compared at 10 steps."""
+    e10, e40 = _separation(W.with_raw_collision(W.oscillating_drop()), [10, 40])
+    assert e10 < 1e-13 and e40 > 1e-11, (e10, e40)
+
+
+def test_static_drop_has_no_horizon():
+    """The 64 x 128 static drop: the runs stay together for all 2000 steps,
+    where parity is compared."""
+    (e2000,) = _separation(W.static_drop(), [2000])
+    assert e2000 < 1e-12, e2000
