@@ -36,7 +36,7 @@ def _volume_radius(phi):
     return (3 * 2 * math.pi * np.sum(r * phi) / (4 * math.pi)) ** (1 / 3)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "mix_fp16"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mix_fp16", "mix_bf16"])
 def test_static_drop_laplace_and_mass(prec):
     """64 x 128 static drop, ratio 1000, 2000 steps: Laplace within 1 %,
     mass drift below 1e-6 (reduced precisions) / 1e-12 (FP64)."""

@@ -117,6 +117,20 @@ def test_horizon_raw_moment_p2_drop():
     assert e10 < 1e-13 and e40 > 1e-11, (e10, e40)
 
 
+@pytest.mark.parametrize("name", ["static_drop_200x100", "ellipsoid_300x150_ratio100"])
+def test_horizon_paper_density_scale(name):
+    """The paper's own static drop (rho_l = 1000, sigma = 1e-3) and its
+    ellipsoid at density ratio 100: the runs separate between 60 and 100
+    steps, where phi overshoots 1 on the axis; parity is compared at 60."""
+    if name.startswith("static"):
+        case = W.base_case(nr=100, nz=200, z_periodic=1, rho_l=1000.0, rho_g=1.0, nu_l=0.1, nu_g=0.1,
+                           sigma=0.001, W=4.0, mobility=0.01, shape="sphere", shape_args=[100.0, 50.0, 4.0])
+    else:
+        case = W.paper_ellipsoid(Rr=30.0, ratio=100.0)
+    e60, e200 = _separation(case, [60, 200])
+    assert e60 < 1e-12 and e200 > 1e-10, (e60, e200)
+
+
 def test_static_drop_has_no_horizon():
     """The 64 x 128 static drop: the runs stay together for all 2000 steps,
     where parity is compared."""

@@ -67,3 +67,70 @@ def test_job_throughput_two_gloo_ranks():
 def test_single_rank_fallback():
     mlups, ms, nodes = shard.job_throughput(1000, 10, 2.0, None)
     assert (ms, nodes) == (2.0, 1000) and abs(mlups - 5.0) < 1e-12
+
+
+def _sim_worker(rank, world, port, steps, out):
+    """Each rank advances its share of a small batch on the FP64 oracle (the
+    CPU stand-in for its GPU) and reports each case's diagnostics and its own
+    measured time; the job's throughput comes from those times."""
+    import time
+
+    import torch.distributed as dist
+
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    oracle.set_threads(1)
+    cases = [c for _, c in sorted(W.small_cases().items())]
+    sizes = [c["nr"] * c["nz"] for c in cases]
+    mine = shard.assign_cases(sizes, world, rank)
+    t0 = time.perf_counter()
+    diags = {}
+    for i in mine:
+        o = oracle.Oracle(dict(cases[i], precision="fp64")).init(W.initial_phi(cases[i]))
+        o.step(steps)
+        diags[i] = o.diagnostics()
+    local_ms = (time.perf_counter() - t0) * 1e3
+    local_nodes = sum(sizes[i] for i in mine)
+    mlups, ms, nodes = shard.job_throughput(local_nodes, steps, local_ms, dist)
+    gathered = [None] * world
+    dist.all_gather_object(gathered, local_ms)
+    out[rank] = (diags, local_ms, mlups, ms, nodes, gathered)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_batch_equals_single_rank_run():
+    """World size 2: the union of the ranks' per-case diagnostics equals the
+    single-rank run bit for bit, every case is advanced exactly once, and the
+    job throughput is all nodes over the slowest rank's measured time."""
+    import oracle
+
+    world, steps = 2, 30
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_sim_worker, args=(r, world, port, steps, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    cases = [c for _, c in sorted(W.small_cases().items())]
+    union = {}
+    for r in range(world):
+        for i, d in out[r][0].items():
+            assert i not in union, "a case advanced on two ranks"
+            union[i] = d
+    assert sorted(union) == list(range(len(cases)))
+    for i, c in enumerate(cases):
+        ref = oracle.Oracle(dict(c, precision="fp64")).init(W.initial_phi(c)).step(steps).diagnostics()
+        assert union[i] == ref, i
+    times = out[0][5]
+    total = sum(c["nr"] * c["nz"] for c in cases)
+    for r in range(world):
+        _, local_ms, mlups, ms, nodes, _ = out[r]
+        assert ms == max(times) and nodes == total
+        assert abs(mlups - total * steps / (ms * 1e-3) / 1e6) < 1e-9 * mlups
