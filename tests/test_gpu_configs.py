@@ -116,11 +116,14 @@ def _configs():
 
 CONFIGS = _configs()
 
-# Bounds on (max, L2) of |phi - phi_oracle| per storage precision.  FP32
-# arithmetic rounds at 6e-8 relative per operation; 16-bit storage rounds every
-# stored population at 2^-11 (FP16) or 2^-8 (BF16) of its deviation, and the
-# interface moves with those errors for hundreds of steps.
-PHI_BOUND = {"fp32": (2e-3, 1e-4), "mix_fp16": (5e-2, 2e-3), "mix_bf16": (0.3, 2e-2)}
+# Bounds on (max, L2) of |phi - phi_oracle| per storage precision, about
+# three times the largest measured value over these configurations (GB300,
+# 1000-2000 steps): FP32 3.7e-3 / 1.9e-4, FP16 1.3e-2 / 4.2e-4, BF16 0.14 /
+# 3.7e-3.  FP32 arithmetic (with the approximate reciprocal and square root)
+# rounds at ~1e-7 per operation; 16-bit storage rounds every stored
+# population at 2^-11 (FP16) or 2^-8 (BF16) of its deviation; the largest
+# errors sit on the axis row, where the 1/r terms are largest.
+PHI_BOUND = {"fp32": (1e-2, 5e-4), "mix_fp16": (4e-2, 1.5e-3), "mix_bf16": (0.4, 1.2e-2)}
 
 
 def _record(row):
