@@ -42,6 +42,10 @@ BYTES_PER_NODE = {
     "mix_fp16": 2 * (8 + 8 * 2 + 9 * 2 + 2 * 4),  # 100
     "mix_bf16": 2 * (8 + 8 * 2 + 9 * 2 + 2 * 4),  # 100
 }
+# The survey's per-node byte count (populations f and g read and written, phi
+# once each way, chi^{n-1} and p^{n-1} read and written), reported beside the
+# narrower count above.
+BYTES_PER_NODE_SURVEY = {"fp64": 352, "fp32": 176, "mix_fp16": 108, "mix_bf16": 108}
 DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf16": "f32 (bf16 storage)"}
 # DRAM bytes per node update of the step kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the nodes of the captured
@@ -51,10 +55,10 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf
 TRAFFIC_B_PER_NODE = {("fp32", 0, "orthogonal"): 164.96}
 # The FP64 step is bound by the FP64 pipe, not by HBM: FP64-pipe thread
 # instructions (DADD + DFMA + DMUL) per node update from one ncu capture
-# (profiles/step_kernel_fp64_batched64cases.md), against the pipe's peak of
-# 2 per SM per cycle x 152 SMs x 2.07 GHz (maximum SM clock).
+# (profiles/step_kernel_fp64_batched64cases.md), against the pipe's rate
+# measured in the same run (lbm_measure_fp64_rate: dependent FP64 FMA chains
+# timed with CUDA events).
 FP64_OPS_PER_NODE = 383.3
-FP64_PIPE_PEAK_GOPS = 2 * 152 * 2.07
 # What the GPU parity tests hold each precision to against the FP64 oracle.
 PARITY_TOL = {
     "fp64": "phi, rho, u, p within 1e-11 (relative max-norm) of the FP64 oracle",
@@ -200,6 +204,38 @@ def cpu_baseline(case: dict, budget_s: float = 15.0):
                       f"({dt:.1f} s, OpenMP over {cores} host threads)"}
 
 
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def run_cpu_table(args):
+    """The FP64 oracle as it stands on this host, single-threaded and on every
+    core, on the 64 x 128 static drop and the 128 x 256 oscillating drop
+    (2000 steps each): one JSON line per run."""
+    import oracle
+    from paper_1810_09299_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    model = cpu_model()
+    for name, case in (("static drop 64x128", W.static_drop()), ("oscillating drop 128x256", W.oscillating_drop())):
+        for threads in (1, cores):
+            oracle.set_threads(threads)
+            o = oracle.Oracle(dict(case, precision="fp64")).init(W.initial_phi(case))
+            steps = args.cpu_steps
+            t0 = time.perf_counter()
+            o.step(steps)
+            dt = time.perf_counter() - t0
+            print(json.dumps({"workload": name, "steps": steps, "threads": threads, "nproc": cores,
+                              "cpu": model, "seconds": dt,
+                              "mlups": case["nr"] * case["nz"] * steps / dt / 1e6}), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -292,6 +328,7 @@ def run_cuda(args):
     peak, peak_kind = measured_peaks()
     per_launch_ms = float(np.mean(times))
     achieved = BYTES_PER_NODE[prec] * nodes / (per_launch_ms * 1e-3) / 1e9
+    ach_survey = BYTES_PER_NODE_SURVEY[prec] * nodes / (per_launch_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -311,13 +348,18 @@ def run_cuda(args):
                                  if (prec, variant, args.collision) in TRAFFIC_B_PER_NODE else None),
                      "traffic_unit": "bytes per launch (ncu capture of 64 cases scaled by node count)",
                      "note": f"peak {peak_kind}; algorithmic bytes {BYTES_PER_NODE[prec]} B/node x {nodes} nodes "
-                             f"per launch / mean CUDA-event launch duration"},
+                             f"per launch / mean CUDA-event launch duration",
+                     "survey_bytes_per_node": BYTES_PER_NODE_SURVEY[prec], "achieved_survey": ach_survey,
+                     "frac_survey": ach_survey / peak},
         "gpu_launches": int(launches),
         # the autotuner restores the state it started from, so d["step"] counts
         # the warm-up and timed steps only
-        "stated_error": {"case0_rel_mass_drift": abs(d["mass"] - mass0) / mass0, "case0_steps": d["step"],
-                         "parity_tolerance": PARITY_TOL[prec]},
+        "stated_error": dict(case_error_vs_fp64(sim, cases[0], int(d["step"]), prec),
+                             case0_rel_mass_drift=abs(d["mass"] - mass0) / mass0, case0_steps=d["step"],
+                             parity_tolerance=PARITY_TOL[prec]),
     }
+    if rank == 0 and not args.no_extra:
+        line["graph"] = graph_leg(sim, torch, nodes, args)
     clocks = clk.summary()
     if clocks:
         line["clocks"] = clocks
@@ -344,6 +386,47 @@ def run_cuda(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def case_error_vs_fp64(sim, case, steps, prec):
+    """Max and L2 (rms over nodes) errors of phi, u_z, u_r and p of the timed
+    case 0 against the FP64 GPU path run from the same initial shape for the
+    same number of steps (the FP64 path matches the FP64 oracle to 1e-11 in
+    the parity tests)."""
+    from paper_1810_09299_gb300 import lbm
+    got = sim.fields(0)
+    ref_sim = lbm.Simulation(dict(case, precision="fp64"))
+    ref_sim.init_phase(0, case["shape"], case["shape_args"])
+    ref_sim.step(steps)
+    ref = ref_sim.fields(0)
+    ref_sim.close()
+    out = {"against": f"FP64 GPU path, case 0 ({case['nr']}x{case['nz']}), {steps} steps"}
+    for k in ("phi", "uz", "ur", "p"):
+        e = got[k] - ref[k]
+        out[k] = {"max": float(np.max(np.abs(e))), "l2": float(np.sqrt(np.mean(e * e))),
+                  "scale": float(np.max(np.abs(ref[k])))}
+    return out
+
+
+def graph_leg(sim, torch, nodes, args):
+    """The same handle stepped by lbm_step(n) with n a multiple of the 32-step
+    captured CUDA graph: one graph launch per 32 steps, timed with CUDA events
+    around the whole call."""
+    n = 64
+    sim.step(n)  # captures the graph (first use) and warms up
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = max(1, min(4, args.steps // n))
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(reps):
+        sim.step(n)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (reps * n)
+    return {"value": nodes / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "steps": reps * n,
+            "launch": "lbm_step(64): two replays of the captured 32-step graph per call"}
 
 
 def e2e(cases, args, torch):
@@ -428,10 +511,13 @@ def batched_other(torch, args, prec, steps, raw=False):
            "bytes_per_node": BYTES_PER_NODE[prec]}
     if prec == "fp64":
         gops = FP64_OPS_PER_NODE * nodes / (ms * 1e-3) / 1e9
-        out["alu_roofline"] = {"bound": "alu", "achieved": gops, "peak": FP64_PIPE_PEAK_GOPS,
-                               "unit": "G FP64-pipe instructions/s", "frac": gops / FP64_PIPE_PEAK_GOPS,
-                               "note": f"{FP64_OPS_PER_NODE} DADD+DFMA+DMUL per node (ncu); "
-                                       "peak 2/SM/cycle x 152 SMs x 2.07 GHz"}
+        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            peak = lbm.measure_fp64_rate(iters=20000) / 1e9
+        out["alu_roofline"] = {"bound": "alu", "achieved": gops, "peak": peak,
+                               "unit": "G FP64-pipe instructions/s", "frac": gops / peak,
+                               "peak_kind": "measured: lbm_measure_fp64_rate (dependent FP64 FMA chains, "
+                                            "CUDA events)", "peak_clocks": clk.summary(),
+                               "note": f"{FP64_OPS_PER_NODE} DADD+DFMA+DMUL per node (ncu)"}
     return out
 
 
@@ -472,10 +558,15 @@ def main():
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--variant", type=int, default=None, help="step-kernel launch shape (default: autotuned)")
     ap.add_argument("--cases", type=int, default=512, help="number of batched cases")
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="time the FP64 oracle on the host (1 thread and all cores) and exit")
+    ap.add_argument("--cpu-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.cpu_table:
+        run_cpu_table(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_cuda(args)

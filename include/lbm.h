@@ -213,6 +213,35 @@ int lbm_case_get_fields(lbm_handle* h, int32_t icase, int32_t mask, double* host
 int lbm_diagnostics(lbm_handle* h, lbm_diag* out);
 int lbm_case_diagnostics(lbm_handle* h, int32_t icase, lbm_diag* out);
 
+/* One liquid drop on the axis (see lbm_case_axis_drops). */
+typedef struct {
+    double z_start, z_end;  /* phi = 1/2 crossings on the axis; z_end < z_start when it wraps */
+    double volume;          /* 2 pi sum r phi over the rows of the drop */
+    double radius;          /* radius of the sphere of that volume */
+} lbm_drop;
+#define LBM_MAX_AXIS_DROPS 64
+
+/* The drops along the axis of case icase: the liquid bodies that a breaking
+ * liquid thread forms (Sec. 3.3), from which its breakup time and the sizes
+ * of its main and satellite drops are read.  Each maximal run of nodes of the
+ * axis row (j = 0) with phi > 1/2 is one drop (its ends: the interpolated
+ * phi = 1/2 crossings, or a z wall plane).  Every row of the case belongs to
+ * one drop: each gas gap on the axis is split at its row of least
+ * sum_j r_j phi (the first such row), and a drop's volume is 2 pi sum r phi over
+ * its rows.  In a z-periodic case the rows wrap around; with phi > 1/2 along
+ * the whole axis the case holds one unbroken body (z_start = 0, z_end = nz).
+ * A thread has broken once the least phi of the axis row falls below 1/2.
+ *   max_drops   0 .. LBM_MAX_AXIS_DROPS: records to write to drops[], in z
+ *               order from the scan start (z = 0, or in a periodic case the
+ *               first gas gap after z = 0).
+ *   n_drops     number of drops found (may exceed max_drops).
+ *   axis_min    NULL, or 2 doubles: the least phi of the axis row and its z.
+ * Computed on the device in FP64 from the fields of lbm_get_fields.
+ * Synchronises.  LBM_ERR_INVALID_ARG for a bad case, count or pointer,
+ * LBM_ERR_STATE before the case's initial condition. */
+int lbm_case_axis_drops(lbm_handle* h, int32_t icase, int32_t max_drops, lbm_drop* drops, int32_t* n_drops,
+                        double* axis_min);
+
 /* Pipelined diagnostics: the record of lbm_case_diagnostics (the quantities
  * Sec. 3.1-3.3 read off the runs), enqueued on the handle's stream without
  * waiting, so that a loop reading one record per step keeps the GPU busy:
@@ -298,6 +327,16 @@ int lbm_diag_reduce_noalloc(const double* d_fields, int32_t nz, int32_t nr, int3
  * not, LBM_ERR_INVALID_ARG for tries < 1 or a NULL pointer.  Synchronises
  * `stream`.  The context stays usable: the kernel leaves no work in flight. */
 int lbm_selftest_bounded_wait(int32_t tries, void* stream, int32_t* device_status_word);
+
+/* Measured throughput of the GPU's FP64 pipe (no paper counterpart: the
+ * denominator of the FP64 step's arithmetic roofline, whose step is bound by
+ * that pipe rather than by memory).  Launches 4 blocks of 256 threads per SM,
+ * each thread running 8 independent chains of `iters` dependent FP64 fused
+ * multiply-adds, after one untimed warm-up launch, and writes the FMA count
+ * over the CUDA-event time of the timed launch to *fma_per_second.  Allocates
+ * and frees a small device buffer; synchronises `stream`.  LBM_ERR_INVALID_ARG
+ * for iters < 1 or a NULL pointer. */
+int lbm_measure_fp64_rate(int32_t iters, void* stream, double* fma_per_second);
 
 /* Release every resource of the handle (NULL is ignored).  No paper
  * counterpart: resource management only. */

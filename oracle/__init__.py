@@ -82,6 +82,7 @@ def lib():
             L.orc_get_aux.argtypes = [ctypes.c_void_p, dp, dp, dp]
             L.orc_set_aux.argtypes = [ctypes.c_void_p, dp, dp, dp]
             L.orc_diagnostics.argtypes = [ctypes.c_void_p, ctypes.POINTER(OrcDiag)]
+            L.orc_axis_drops.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, ip, dp]
             L.orc_step_count.restype = ctypes.c_int64
             L.orc_step_count.argtypes = [ctypes.c_void_p]
             L.orc_set_threads.argtypes = [ctypes.c_int]
@@ -275,6 +276,17 @@ class Oracle:
     def set_aux(self, chi_z, chi_r, p_prev):
         a, b, c = _c(chi_z), _c(chi_r), _c(p_prev)
         lib().orc_set_aux(self._h, _p(a), _p(b), _p(c))
+
+    def axis_drops(self, max_drops: int = 64):
+        """Drops on the axis row: (list of dicts z_start, z_end, volume, radius;
+        number found; (least axis phi, its z))."""
+        out = np.zeros(4 * max(1, max_drops))
+        n = ctypes.c_int(0)
+        amin = np.zeros(2)
+        lib().orc_axis_drops(self._h, int(max_drops), _p(out), ctypes.byref(n), _p(amin))
+        keys = ("z_start", "z_end", "volume", "radius")
+        drops = [{k: float(out[4 * m + i]) for i, k in enumerate(keys)} for m in range(min(n.value, max_drops))]
+        return drops, int(n.value), (float(amin[0]), float(amin[1]))
 
     def diagnostics(self) -> dict:
         d = OrcDiag()

@@ -721,3 +721,136 @@ int orc_diagnostics(orc_state* s, orc_diag* out)
     free(ph); free(rh); free(uz); free(ur); free(p);
     return 0;
 }
+
+/* Drops on the axis (the bodies a breaking thread forms, Sec. 3.3): maximal
+ * runs of axis nodes (j = 0) with phi > 1/2.  Written in two passes: first the
+ * runs, then for each gas gap between two runs the row of least sum_j r phi
+ * (first such row) where the rows are split between the two drops; a drop's
+ * volume is 2 pi sum r phi over its rows.  In a walled case the rows before the
+ * first run and after the last one belong to those runs; in a periodic case
+ * the gap that wraps around is split like the others. */
+int orc_axis_drops(orc_state* s, int max_drops, double* out, int* n_drops, double* axis_min)
+{
+    const int nr = s->prm.nr, nz = s->prm.nz, zper = s->prm.z_periodic;
+    const double two_pi = 2.0 * acos(-1.0);
+    double* ph = (double*)malloc(s->n * sizeof(double));
+    double* w = (double*)malloc((size_t)nz * sizeof(double));
+    int* rs = (int*)malloc((size_t)(nz + 1) * sizeof(int)); /* first row of each run */
+    int* re = (int*)malloc((size_t)(nz + 1) * sizeof(int)); /* last row of each run */
+    if (!ph || !w || !rs || !re) {
+        free(ph); free(w); free(rs); free(re);
+        return -1;
+    }
+    orc_fields(s, ph, NULL, NULL, NULL, NULL);
+    for (int k = 0; k < nz; ++k) {
+        w[k] = 0.0;
+        for (int j = 0; j < nr; ++j) w[k] += radius(j) * ph[(size_t)k * nr + j];
+    }
+    int kmin = 0;
+    for (int k = 1; k < nz; ++k)
+        if (ph[(size_t)k * nr] < ph[(size_t)kmin * nr]) kmin = k;
+    if (axis_min) {
+        axis_min[0] = ph[(size_t)kmin * nr];
+        axis_min[1] = kmin + 0.5;
+    }
+#define LIQ(k) (ph[(size_t)(k) * nr] > 0.5)
+    /* pass 1: runs, in rows 0 .. nz-1 */
+    int nruns = 0;
+    for (int k = 0; k < nz; ++k) {
+        if (LIQ(k) && (k == 0 || !LIQ(k - 1))) rs[nruns] = k;
+        if (LIQ(k) && (k == nz - 1 || !LIQ(k + 1))) re[nruns++] = k;
+    }
+    /* periodic: a run through z = 0 and one through z = nz are one drop */
+    int all_liquid = (nruns == 1 && rs[0] == 0 && re[0] == nz - 1);
+    if (zper && nruns >= 2 && rs[0] == 0 && re[nruns - 1] == nz - 1) {
+        rs[0] = rs[nruns - 1];   /* the merged drop starts in the last run */
+        nruns -= 1;
+        /* rotate so that the merged drop comes last (scan order starts after a gap) */
+        int s0 = rs[0], e0 = re[0];
+        for (int m = 0; m + 1 < nruns; ++m) { rs[m] = rs[m + 1]; re[m] = re[m + 1]; }
+        rs[nruns - 1] = s0;
+        re[nruns - 1] = e0;
+    } else if (zper && nruns >= 1 && !all_liquid) {
+        /* order the runs from the first gap after z = 0: a run starting at row 0
+         * (the gap before it wraps) is kept last */
+        if (rs[0] == 0) {
+            int s0 = rs[0], e0 = re[0];
+            for (int m = 0; m + 1 < nruns; ++m) { rs[m] = rs[m + 1]; re[m] = re[m + 1]; }
+            rs[nruns - 1] = s0;
+            re[nruns - 1] = e0;
+        }
+    }
+    *n_drops = nruns;
+    if (nruns == 0) {
+        free(ph); free(w); free(rs); free(re);
+        return 0;
+    }
+    if (all_liquid && zper) {
+        double v = 0.0;
+        for (int k = 0; k < nz; ++k) v += w[k];
+        if (max_drops > 0) {
+            out[0] = 0.0;
+            out[1] = nz;
+            out[2] = two_pi * v;
+            out[3] = cbrt(3.0 * out[2] / (4.0 * acos(-1.0)));
+        }
+        free(ph); free(w); free(rs); free(re);
+        return 0;
+    }
+    /* pass 2: the cut row of the gap after each run (cyclic in periodic cases);
+     * walled: the last run takes every row up to nz */
+    for (int m = 0; m < nruns && m < max_drops; ++m) {
+        double* d = out + 4 * m;
+        /* ends: crossings between the run's outer rows and the gas rows next to them */
+        int kb = rs[m] - 1, ka = re[m] + 1;
+        if (!zper && rs[m] == 0) d[0] = 0.0;
+        else {
+            int k0 = (kb + nz) % nz;
+            double a = ph[(size_t)k0 * nr], b = ph[(size_t)rs[m] * nr];
+            double z = (kb + 0.5) + (0.5 - a) / (b - a);
+            d[0] = z < 0.0 ? z + nz : z;
+        }
+        if (!zper && re[m] == nz - 1) d[1] = nz;
+        else {
+            int k1 = ka % nz;
+            double a = ph[(size_t)re[m] * nr], b = ph[(size_t)k1 * nr];
+            double z = (re[m] + 0.5) + (0.5 - a) / (b - a);
+            d[1] = z >= nz ? z - nz : z;
+        }
+    }
+    /* cut rows: cut[m] = first row of drop m's share (rows cut[m] .. cut[m+1]-1, cyclic) */
+    int* cut = (int*)malloc((size_t)(nruns + 1) * sizeof(int));
+    if (!cut) {
+        free(ph); free(w); free(rs); free(re);
+        return -1;
+    }
+    for (int m = 0; m < nruns; ++m) {
+        /* the gap before run m: from the row after the previous run's end */
+        int prev = (m == 0) ? (zper ? nruns - 1 : -1) : m - 1;
+        if (prev < 0) {
+            cut[m] = 0;
+            continue;
+        }
+        int g0 = (re[prev] + 1) % nz, len = (rs[m] - g0 + nz) % nz;
+        int best = g0;
+        for (int q = 1; q < len; ++q) {
+            int k = (g0 + q) % nz;
+            if (w[k] < w[best]) best = k;
+        }
+        cut[m] = best;
+    }
+    for (int m = 0; m < nruns && m < max_drops; ++m) {
+        int a = cut[m];
+        int b = (m + 1 < nruns) ? cut[m + 1] : (zper ? cut[0] : nz);
+        int len = zper ? ((b - a + nz) % nz) : (b - a);
+        if (zper && len == 0) len = nz;
+        double v = 0.0;
+        for (int q = 0; q < len; ++q) v += w[(a + q) % nz];
+        out[4 * m + 2] = two_pi * v;
+        out[4 * m + 3] = cbrt(3.0 * out[4 * m + 2] / (4.0 * acos(-1.0)));
+    }
+#undef LIQ
+    free(cut);
+    free(ph); free(w); free(rs); free(re);
+    return 0;
+}

@@ -76,6 +76,10 @@ int orc_set_populations(orc_state* s, const double* f, const double* g);
 int orc_get_aux(const orc_state* s, double* chi_z, double* chi_r, double* p_prev);
 int orc_set_aux(orc_state* s, const double* chi_z, const double* chi_r, const double* p_prev);
 int orc_diagnostics(orc_state* s, orc_diag* out);
+/* Drops on the axis row (phi > 1/2 runs; Sec. 3.3): *n_drops found, out[4 m ..]
+ * = (z_start, z_end, volume, equivalent radius) for m < max_drops; axis_min
+ * (may be NULL) = (least phi of the axis row, its z). */
+int orc_axis_drops(orc_state* s, int max_drops, double* out, int* n_drops, double* axis_min);
 int64_t orc_step_count(const orc_state* s);
 void orc_set_threads(int nthreads);
 

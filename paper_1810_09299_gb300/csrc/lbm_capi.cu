@@ -97,6 +97,9 @@ struct lbm_sim {
     double* state = nullptr;    // [21][nz][nr]
     double* partials = nullptr;
     double* diag_out = nullptr;
+    double* axis_rows = nullptr;   // nz doubles of the tallest case
+    double* axis_out = nullptr;    // the drops record, 3 + 4 * kMaxAxisDrops doubles
+    double* axis_host = nullptr;   // pinned copy of axis_out
     // pinned host staging for small reads (a diagnostics record and the
     // status word), so that they return with one synchronisation
     double* host_small = nullptr;
@@ -297,6 +300,8 @@ void release(lbm_sim* h) {
     h->host_small = nullptr;
     if (h->slot_status) cudaFreeHost(h->slot_status);
     h->slot_status = nullptr;
+    if (h->axis_host) cudaFreeHost(h->axis_host);
+    h->axis_host = nullptr;
     for (cudaEvent_t& e : h->diag_ev) {
         if (e) cudaEventDestroy(e);
         e = nullptr;
@@ -371,7 +376,9 @@ int create_impl(const lbm_params* cases, int32_t n, void* stream, lbm_handle** o
     h->ncases = n;
     h->prm.assign(cases, cases + n);
     int64_t off = 0;
+    int max_nz = 0;
     for (int c = 0; c < n; ++c) {
+        max_nz = std::max(max_nz, cases[c].nz);
         h->cases.push_back(make_case(cases[c], off));
         off += (int64_t)h->cases[c].nz * h->cases[c].pitch;
         h->max_nodes = std::max<int64_t>(h->max_nodes, (int64_t)cases[c].nz * cases[c].nr);
@@ -399,10 +406,17 @@ int create_impl(const lbm_params* cases, int32_t n, void* stream, lbm_handle** o
     A((void**)&h->state, 21 * (size_t)h->max_nodes * sizeof(double));
     A((void**)&h->partials, diag_partials_size() * sizeof(double));
     A((void**)&h->diag_out, 16 * sizeof(double));
+    A((void**)&h->axis_rows, (size_t)max_nz * sizeof(double));
+    A((void**)&h->axis_out, (3 + 4 * kMaxAxisDrops) * sizeof(double));
     A((void**)&h->D.status, 128);
     if (rc == LBM_OK && cudaMallocHost((void**)&h->host_small, 16 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         h->host_small = nullptr;
+        rc = LBM_ERR_OOM;
+    }
+    if (rc == LBM_OK && cudaMallocHost((void**)&h->axis_host, (3 + 4 * kMaxAxisDrops) * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        h->axis_host = nullptr;
         rc = LBM_ERR_OOM;
     }
     if (rc == LBM_OK && cudaMallocHost((void**)&h->slot_status, LBM_DIAG_SLOTS * sizeof(int)) != cudaSuccess) {
@@ -716,6 +730,42 @@ int lbm_case_diagnostics(lbm_handle* h, int32_t icase, lbm_diag* out) {
 }
 
 int lbm_diagnostics(lbm_handle* h, lbm_diag* out) { return lbm_case_diagnostics(h, 0, out); }
+
+int lbm_case_axis_drops(lbm_handle* h, int32_t icase, int32_t max_drops, lbm_drop* drops, int32_t* n_drops,
+                        double* axis_min) {
+    static_assert(sizeof(lbm_drop) == 4 * sizeof(double), "drop record layout");
+    static_assert(LBM_MAX_AXIS_DROPS == kMaxAxisDrops, "drop capacity");
+    int rc = enter(h);
+    if (rc != LBM_OK) return rc;
+    if (check_case(h, icase) != LBM_OK || !n_drops || max_drops < 0 || max_drops > kMaxAxisDrops ||
+        (max_drops > 0 && !drops))
+        return LBM_ERR_INVALID_ARG;
+    if (!h->initialized[icase]) return LBM_ERR_STATE;
+    rc = check_status(h);
+    if (rc != LBM_OK) return rc;
+    rc = join_diagnostics(h);
+    if (rc != LBM_OK) return rc;
+    rc = cuda_ok(h, launch_fields_any(h, icase, h->stream));
+    if (rc != LBM_OK) return rc;
+    const lbm_params& p = h->prm[icase];
+    rc = cuda_ok(h, launch_axis_drops(h->fields, p.nz, p.nr, p.z_periodic, max_drops, h->axis_rows, h->axis_out,
+                                      h->stream));
+    if (rc != LBM_OK) return rc;
+    rc = cuda_ok(h, cudaMemcpyAsync(h->axis_host, h->axis_out, (3 + 4 * (size_t)max_drops) * sizeof(double),
+                                    cudaMemcpyDeviceToHost, h->stream));
+    if (rc != LBM_OK) return rc;
+    rc = cuda_ok(h, cudaStreamSynchronize(h->stream));
+    if (rc != LBM_OK) return rc;
+    const int n = (int)h->axis_host[0];
+    *n_drops = n;
+    if (axis_min) {
+        axis_min[0] = h->axis_host[1];
+        axis_min[1] = h->axis_host[2];
+    }
+    const int m = n < max_drops ? n : max_drops;
+    if (m > 0) std::memcpy(drops, h->axis_host + 3, (size_t)m * sizeof(lbm_drop));
+    return LBM_OK;
+}
 
 int lbm_case_diagnostics_enqueue(lbm_handle* h, int32_t icase, lbm_diag* host_out, int32_t slot) {
     int rc = enter(h);

@@ -254,6 +254,166 @@ __global__ void __launch_bounds__(kFinalThreads) diag_final_kernel(const double*
     out[10] = sres[17];
 }
 
+// ---------------------------------------------------------------- drops on the axis
+// The liquid bodies a breaking thread forms (Sec. 3.3), read off the axis row
+// j = 0: every maximal run of axis nodes with phi > 1/2 is one drop.  The rows
+// of the case are split between the drops at one row inside each gas gap (the
+// row of least r-weighted phi of the gap, first on ties), so every row belongs
+// to exactly one drop and a drop's volume is 2 pi sum r phi over its rows.
+// Its ends are the linearly interpolated phi = 1/2 crossings on the axis (a
+// wall plane where the run reaches a z wall).  In a periodic case the rows
+// wrap; with no gap at all the whole axis is one unbroken body.
+//
+// Output (FP64): out[0] = number of drops, out[1] = min phi on the axis row,
+// out[2] = row of that minimum + 1/2 (its z), then for each of the first
+// min(number, max_drops) drops in z order (z_start, z_end, volume, radius of
+// the sphere of that volume); z_end < z_start for a drop that wraps a periodic
+// boundary.  rows: scratch of nz doubles.
+constexpr int kAxisThreads = 256;
+
+__device__ __forceinline__ double axis_phi(const double* F, int nr, int k) { return F[(int64_t)k * nr]; }
+
+// z of the phi = 1/2 crossing between axis rows k and k + 1 (k + 1 taken
+// modulo nz, positions unwrapped: z may exceed nz by less than one row).
+__device__ __forceinline__ double axis_crossing(const double* F, int nz, int nr, int k) {
+    const double a = axis_phi(F, nr, k), b = axis_phi(F, nr, (k + 1) % nz);
+    return (k + 0.5) + (0.5 - a) / (b - a);
+}
+
+__global__ void __launch_bounds__(kAxisThreads) axis_drops_kernel(const double* __restrict__ F, int nz, int nr,
+                                                                  int zper, int max_drops,
+                                                                  double* __restrict__ rows,
+                                                                  double* __restrict__ out) {
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+        double s = 0.0;
+        // separately rounded products and sums in r order (no contraction)
+        for (int j = 0; j < nr; ++j) s = __dadd_rn(s, __dmul_rn(j + 0.5, F[(int64_t)k * nr + j]));
+        rows[k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double two_pi = 6.283185307179586;
+    double pmin = INFINITY;
+    int kmin = 0;
+    int start = -1;  // a gas row of the axis to start the scan at (periodic)
+    for (int k = 0; k < nz; ++k) {
+        const double v = axis_phi(F, nr, k);
+        if (v < pmin) {
+            pmin = v;
+            kmin = k;
+        }
+        if (start < 0 && !(v > 0.5)) start = k;
+    }
+    out[1] = pmin;
+    out[2] = kmin + 0.5;
+    const auto put = [&](int drop, int field, double v) {
+        if (drop < max_drops) out[3 + 4 * drop + field] = v;
+    };
+    const auto close_drop = [&](int drop, double v) {
+        put(drop, 2, two_pi * v);
+        put(drop, 3, cbrt(3.0 * two_pi * v / (4.0 * M_PI)));
+    };
+    if (start < 0) {  // liquid along the whole axis: one unbroken body
+        double vol = 0.0;
+        for (int k = 0; k < nz; ++k) vol += rows[k];
+        out[0] = 1.0;
+        put(0, 0, 0.0);
+        put(0, 1, (double)nz);
+        close_drop(0, vol);
+        return;
+    }
+    if (zper) {
+        // start the scan at the first row of a gas gap, so that the rows
+        // before it (cyclically) end the last drop
+        int n = 0;
+        while (n < nz && !(axis_phi(F, nr, (start + nz - 1) % nz) > 0.5)) {
+            start = (start + nz - 1) % nz;
+            ++n;
+        }
+        if (n == nz) {  // gas along the whole axis: no drop
+            out[0] = 0.0;
+            return;
+        }
+    } else {
+        start = 0;
+    }
+    // One pass over the rows in scan order.  Inside a gap the rows before its
+    // lightest row go to the drop before the gap, the rest to the drop after it.
+    int ndrops = 0;
+    double vol = 0.0;                      // rows of the current drop so far
+    double gap_before = 0.0, gap_after = 0.0, gap_min = 0.0;
+    double lead_before = 0.0;              // periodic: first gap's share of the last drop
+    bool in_gap = false, first_row = true;
+    for (int i = 0; i < nz; ++i) {
+        const int k = zper ? (start + i) % nz : i;
+        const int kp = (k + nz - 1) % nz;  // the row before k (cyclically)
+        const bool liquid = axis_phi(F, nr, k) > 0.5;
+        if (!liquid) {
+            if (!in_gap) {
+                // a gap opens: the drop before it (if any) ends before this row
+                if (!first_row) {
+                    double ze = axis_crossing(F, nz, nr, kp);
+                    if (ze >= nz) ze -= nz;
+                    put(ndrops - 1, 1, ze);
+                }
+                in_gap = true;
+                gap_before = 0.0;
+                gap_after = rows[k];
+                gap_min = rows[k];
+            } else if (rows[k] < gap_min) {
+                gap_before += gap_after;
+                gap_after = rows[k];
+                gap_min = rows[k];
+            } else {
+                gap_after += rows[k];
+            }
+        } else {
+            if (in_gap || first_row) {
+                // a drop starts at this row
+                if (ndrops > 0) {
+                    close_drop(ndrops - 1, vol + gap_before);
+                    vol = gap_after;
+                } else {
+                    // the first drop: a leading gap of a walled case is all its;
+                    // in a periodic case the part before the cut wraps to the last drop
+                    if (zper) {
+                        lead_before = gap_before;
+                        vol = gap_after;
+                    } else {
+                        vol = gap_before + gap_after;
+                    }
+                }
+                double zs = 0.0;  // a drop touching the wall z = 0 starts at the wall plane
+                if (!(first_row && !zper)) {
+                    zs = axis_crossing(F, nz, nr, kp);
+                    if (zs >= nz) zs -= nz;
+                }
+                put(ndrops, 0, zs);
+                ++ndrops;
+                in_gap = false;
+                gap_before = gap_after = 0.0;
+            }
+            vol += rows[k];
+        }
+        first_row = false;
+    }
+    if (ndrops > 0) {
+        if (zper) {
+            // the scan started at a gap's first row, so it ends inside the last drop
+            double ze = axis_crossing(F, nz, nr, (start + nz - 1) % nz);
+            if (ze >= nz) ze -= nz;
+            put(ndrops - 1, 1, ze);
+            close_drop(ndrops - 1, vol + lead_before);
+        } else if (in_gap) {
+            close_drop(ndrops - 1, vol + gap_before + gap_after);
+        } else {
+            put(ndrops - 1, 1, (double)nz);  // the drop reaches the wall z = nz
+            close_drop(ndrops - 1, vol);
+        }
+    }
+    out[0] = (double)ndrops;
+}
+
 // ---------------------------------------------------------------- shapes
 struct ShapeArgs {
     double a[8];
@@ -312,6 +472,12 @@ cudaError_t launch_diag(const double* fields, int nz, int nr, int zper, double s
     return cudaGetLastError();
 }
 
+cudaError_t launch_axis_drops(const double* fields, int nz, int nr, int zper, int max_drops, double* rows, double* out,
+                              cudaStream_t st) {
+    axis_drops_kernel<<<1, kAxisThreads, 0, st>>>(fields, nz, nr, zper, max_drops, rows, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_shape(int shape, const double* args, int nargs, int nz, int nr, double* phi0, cudaStream_t st) {
     ShapeArgs A{};
     for (int i = 0; i < nargs && i < 8; ++i) A.a[i] = args[i];
@@ -347,6 +513,64 @@ extern "C" int lbm_selftest_bounded_wait(int32_t tries, void* stream, int32_t* d
         return LBM_ERR_CUDA;
     }
     return st != 0 ? LBM_ERR_TIMEOUT : LBM_OK;
+}
+
+// ---------------------------------------------------------------- FP64 pipe rate
+// Throughput probe of the FP64 pipe (no paper counterpart): every thread runs
+// kChains independent chains of dependent FP64 fused multiply-adds, enough
+// independent work per warp to keep the pipe busy, and writes one sum so the
+// work is not removed.  The rate is the FMA count over the CUDA-event time of
+// the launch.
+namespace {
+constexpr int kFmaChains = 8;
+__global__ void __launch_bounds__(256) dfma_rate_kernel(int iters, double a, double b, double* out) {
+    double x[kFmaChains];
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) x[c] = (double)(threadIdx.x + c) * 1e-3;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kFmaChains; ++c) x[c] = fma(x[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) s += x[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+}  // namespace
+
+extern "C" int lbm_measure_fp64_rate(int32_t iters, void* stream, double* fma_per_second) {
+    if (iters < 1 || !fma_per_second) return LBM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    const int blocks = 4 * sms, threads = 256;
+    double* out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = LBM_OK;
+    if (cudaMalloc(&out, (size_t)blocks * threads * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_OOM;
+    }
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = LBM_ERR_CUDA;
+    // one warm-up launch, then the timed one
+    for (int rep = 0; rep < 2 && rc == LBM_OK; ++rep) {
+        if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) rc = LBM_ERR_CUDA;
+        dfma_rate_kernel<<<blocks, threads, 0, st>>>(iters, 0.999999, 1e-7, out);
+        if (cudaGetLastError() != cudaSuccess) rc = LBM_ERR_CUDA;
+        if (rep == 1 && rc == LBM_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = LBM_ERR_CUDA;
+    }
+    float ms = 0.0f;
+    if (rc == LBM_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = LBM_ERR_CUDA;
+    if (rc == LBM_OK) *fma_per_second = (double)blocks * threads * kFmaChains * (double)iters / (ms * 1e-3);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    if (rc != LBM_OK) cudaGetLastError();
+    return rc;
 }
 
 // ---------------------------------------------------------------- allocation-free reduction

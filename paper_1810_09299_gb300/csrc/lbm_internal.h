@@ -72,6 +72,12 @@ int diag_partials_size();
 cudaError_t launch_diag(const double* fields, int nz, int nr, int zper, double step, double* partials,
                         double* out, cudaStream_t st);
 
+// Drops on the axis row (lbm_diag.cu): out[3 + 4 * kMaxAxisDrops] doubles,
+// rows: nz doubles of scratch.
+constexpr int kMaxAxisDrops = 64;
+cudaError_t launch_axis_drops(const double* fields, int nz, int nr, int zper, int max_drops, double* rows, double* out,
+                              cudaStream_t st);
+
 // Initial shapes (lbm_diag.cu): phi0 [nz][nr] on the device.
 cudaError_t launch_shape(int shape, const double* args, int nargs, int nz, int nr, double* phi0, cudaStream_t st);
 

@@ -37,7 +37,9 @@ EXPORTS = (
     "lbm_checkpoint_load", "lbm_autotune", "lbm_set_variant", "lbm_num_variants",
     "lbm_kernel_launches", "lbm_destroy", "lbm_strerror", "lbm_diag_reduce_noalloc",
     "lbm_selftest_bounded_wait", "lbm_case_diagnostics_enqueue", "lbm_diagnostics_wait", "lbm_init_phase_all",
+    "lbm_case_axis_drops", "lbm_measure_fp64_rate",
 )
+MAX_AXIS_DROPS = 64
 DIAG_SLOTS = 4
 
 
@@ -58,6 +60,10 @@ class LbmDiag(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "step", "mass", "kinetic", "z_centroid", "dp", "umax", "phi_min", "phi_max",
         "axis_half_length", "radial_half_length", "nonfinite")]
+
+
+class LbmDrop(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("z_start", "z_end", "volume", "radius")]
 
 
 class LbmError(RuntimeError):
@@ -107,6 +113,8 @@ def lib():
         "lbm_case_diagnostics_enqueue": (ctypes.c_int, [vp, i32, ctypes.POINTER(LbmDiag), i32]),
         "lbm_diagnostics_wait": (ctypes.c_int, [vp, i32]),
         "lbm_init_phase_all": (ctypes.c_int, [vp, dp]),
+        "lbm_case_axis_drops": (ctypes.c_int, [vp, i32, i32, ctypes.POINTER(LbmDrop), ctypes.POINTER(i32), dp]),
+        "lbm_measure_fp64_rate": (ctypes.c_int, [i32, vp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -258,6 +266,18 @@ class Simulation:
         out["status"] = rc
         return out
 
+    def axis_drops(self, icase: int = 0, max_drops: int = MAX_AXIS_DROPS):
+        """The drops along the axis (lbm_case_axis_drops): a list of dicts
+        (z_start, z_end, volume, radius) in scan order, the number of drops
+        found, and (least phi on the axis row, its z)."""
+        arr = (LbmDrop * max(1, max_drops))()
+        n = ctypes.c_int32(0)
+        amin = np.zeros(2)
+        _check(lib().lbm_case_axis_drops(self._h, icase, max_drops, arr, ctypes.byref(n), _dp(amin)),
+               "lbm_case_axis_drops")
+        drops = [{k: getattr(arr[i], k) for k, _ in LbmDrop._fields_} for i in range(min(n.value, max_drops))]
+        return drops, int(n.value), (float(amin[0]), float(amin[1]))
+
     def diagnostics_enqueue(self, icase: int, out: "LbmDiag", slot: int):
         """Enqueue case icase's record into `out` (keep it alive, and pinned for
         the copy to be asynchronous, until diagnostics_wait(slot))."""
@@ -302,6 +322,14 @@ class Simulation:
     @property
     def kernel_launches(self) -> int:
         return int(lib().lbm_kernel_launches(self._h))
+
+
+def measure_fp64_rate(iters: int = 20000, stream=None) -> float:
+    """FP64 fused multiply-adds per second the GPU sustains (lbm_measure_fp64_rate)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().lbm_measure_fp64_rate(int(iters), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(out)),
+           "lbm_measure_fp64_rate")
+    return float(out.value)
 
 
 def num_variants() -> int:

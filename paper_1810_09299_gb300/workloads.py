@@ -172,6 +172,28 @@ def thread_breakup(nr=64, R0=20.0, k_wave=0.7, amp_frac=0.1, seed=None, **kw):
     return c
 
 
+def paper_thread(wavelength=600, ratio=100.0, **kw):
+    """The paper's liquid thread (Sec. 3.3): an N_z x N_r = wavelength x 200
+    domain, periodic in z as in its static and oscillating drop tests,
+    Eq. 47 with R = 60 and d = 0.1 R cos(2 pi z / wavelength); sigma = 0.3,
+    W = 4, M = 0.01, nu_l = nu_g = 0.1, the paper's rates, in its density
+    scale rho_g = 1, rho_l = ratio.  Wavelengths 600, 1200, 1800 give the wave
+    numbers k = 2 pi R / wavelength = 0.63, 0.31, 0.21 whose breakup times the
+    paper prints."""
+    R = 60.0
+    c = base_case(nr=200, nz=int(wavelength), z_periodic=1, rho_l=float(ratio), rho_g=1.0, nu_l=0.1, nu_g=0.1,
+                  sigma=0.3, W=4.0, mobility=0.01)
+    c.update(shape="thread", shape_args=[R, 0.1 * R, float(wavelength), 0.0, 4.0])
+    c.update(kw)
+    c["shape_args"][-1] = c["W"]
+    return c
+
+
+def capillary_time(R, rho_l, sigma):
+    """sqrt(R^3 rho_l / sigma), the time unit of Sec. 3.3."""
+    return math.sqrt(R ** 3 * rho_l / sigma)
+
+
 def rising_bubble(nr=256, nz=1024, R=32.0, zc=128.0, **kw):
     """Bubble R = 32 on the axis at z = 128: rho ratio 1000, W = 5.
     With nu_l = 0.08: Eo = g drho D^2 / sigma = 10 and

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _header_functions():
     src = open(os.path.join(ROOT, "include", "lbm.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -60,6 +60,8 @@ def test_binding_fields_follow_the_header():
     """The ctypes mirrors of lbm_params and lbm_diag name the header's fields in its order."""
     assert [f[0] for f in lbm.LbmParams._fields_] == _header_struct_fields("lbm_params")
     assert [f[0] for f in lbm.LbmDiag._fields_] == _header_struct_fields("lbm_diag")
+    assert [f[0] for f in lbm.LbmDrop._fields_] == _header_struct_fields("lbm_drop")
+    assert ctypes.sizeof(lbm.LbmDrop) == 4 * 8
 
 
 def test_strerror_and_static_queries(L):
