@@ -173,13 +173,18 @@ cudaError_t launch_fields_any(lbm_sim* h, int icase, cudaStream_t st) {
     }
 }
 
+// Initial condition from dense phi0: of case icase alone (phi0 holds its
+// [nz][nr]), or with icase < 0 of every case (phi0 holds all of them in order).
 cudaError_t launch_init_any(lbm_sim* h, int icase, const double* phi0) {
-    const CaseDev& C = h->cases[icase];
+    const TileDev* t = icase < 0 ? h->tiles_d[0] : h->ftiles_d[icase];
+    const int n = icase < 0 ? h->ntiles[0] : h->nftiles[icase];
+    const int64_t base = icase < 0 ? 0 : h->cases[icase].dense_off;
+    static_assert(kVariantTZ[0] == 8, "the initial condition covers 8-row tiles");
     switch (h->precision) {
-        case LBM_FP64: return launch_init_f64(h->D, h->parity, C, phi0, h->stream);
-        case LBM_FP32: return launch_init_f32(h->D, h->parity, C, phi0, h->stream);
-        case LBM_MIX_FP16: return launch_init_h16(h->D, h->parity, C, phi0, h->stream);
-        default: return launch_init_b16(h->D, h->parity, C, phi0, h->stream);
+        case LBM_FP64: return launch_init_f64(h->D, h->parity, t, n, phi0, base, h->stream);
+        case LBM_FP32: return launch_init_f32(h->D, h->parity, t, n, phi0, base, h->stream);
+        case LBM_MIX_FP16: return launch_init_h16(h->D, h->parity, t, n, phi0, base, h->stream);
+        default: return launch_init_b16(h->D, h->parity, t, n, phi0, base, h->stream);
     }
 }
 
@@ -240,8 +245,9 @@ int rate_pattern(const lbm_params& p) {
     return raw ? kRatesPaperRaw : kRatesPaper;
 }
 
-CaseDev make_case(const lbm_params& p, int64_t off) {
+CaseDev make_case(const lbm_params& p, int64_t off, int64_t dense_off) {
     CaseDev C{};
+    C.dense_off = dense_off;
     C.nr = p.nr;
     C.nz = p.nz;
     C.pitch = (p.nr + 31) / 32 * 32;
@@ -375,11 +381,12 @@ int create_impl(const lbm_params* cases, int32_t n, void* stream, lbm_handle** o
     h->precision = cases[0].precision;
     h->ncases = n;
     h->prm.assign(cases, cases + n);
-    int64_t off = 0;
+    int64_t off = 0, dense = 0;
     int max_nz = 0;
     for (int c = 0; c < n; ++c) {
         max_nz = std::max(max_nz, cases[c].nz);
-        h->cases.push_back(make_case(cases[c], off));
+        h->cases.push_back(make_case(cases[c], off, dense));
+        dense += (int64_t)cases[c].nz * cases[c].nr;
         off += (int64_t)h->cases[c].nz * h->cases[c].pitch;
         h->max_nodes = std::max<int64_t>(h->max_nodes, (int64_t)cases[c].nz * cases[c].nr);
     }
@@ -634,11 +641,8 @@ int lbm_init_phase_all(lbm_handle* h, const double* host_phi) {
     }
     rc = cuda_ok(h, cudaMemcpyAsync(h->phi0_all, host_phi, (size_t)total * sizeof(double), cudaMemcpyHostToDevice,
                                     h->stream));
-    int64_t o = 0;
-    for (int c = 0; c < h->ncases && rc == LBM_OK; ++c) {
-        rc = cuda_ok(h, launch_init_any(h, c, h->phi0_all + o));
-        o += (int64_t)h->prm[c].nz * h->prm[c].nr;
-    }
+    // one launch over the 8-row tiles of every case
+    if (rc == LBM_OK) rc = cuda_ok(h, launch_init_any(h, -1, h->phi0_all));
     if (rc != LBM_OK) return rc;
     for (int c = 0; c < h->ncases; ++c) {
         h->case_steps[c] = 0;

@@ -66,7 +66,7 @@ struct CaseDev {
     int64_t off;        // node offset of the case (see above)
     int32_t plane;      // nz * pitch
     int32_t collision;  // 0: orthogonal moments (M, Sec. 2.2); 1: raw moments (see raw_from_ortho)
-    int32_t pad2[2];
+    int64_t dense_off;  // first node of the case in the dense concatenation of every case's [nz][nr]
     // the FP32 parameters first, 16-byte aligned (measured -0.45 % on the
     // mixed FP16 step against the FP64 block first; FP32 unchanged)
     CaseReal<float> pf;

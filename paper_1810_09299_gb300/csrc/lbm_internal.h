@@ -41,8 +41,8 @@ struct DeviceState {
                                    cudaStream_t st);                                                               \
     cudaError_t launch_fields_##NAME(const DeviceState& D, int parity, const TileDev* tiles, int ntiles,            \
                                      double* out, cudaStream_t st);                                                \
-    cudaError_t launch_init_##NAME(const DeviceState& D, int parity, const CaseDev& C, const double* phi0,          \
-                                   cudaStream_t st);                                                               \
+    cudaError_t launch_init_##NAME(const DeviceState& D, int parity, const TileDev* tiles8, int ntiles,             \
+                                   const double* phi0, int64_t base, cudaStream_t st);                             \
     cudaError_t launch_get_state_##NAME(const DeviceState& D, int parity, const CaseDev& C, double* f, double* g,   \
                                         double* aux, cudaStream_t st);                                             \
     cudaError_t launch_set_state_##NAME(const DeviceState& D, int parity, const CaseDev& C, const double* f,        \

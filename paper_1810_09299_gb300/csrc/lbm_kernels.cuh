@@ -53,14 +53,20 @@ __device__ __forceinline__ void ring_cell(int q, int& a, int& b) {
 // 4 CTAs (64 registers, no spill) that measured -3.4 % in FP32, -2.2 % in
 // FP16 and -5.1 % in BF16 storage with the paper's collision, with the same
 // results.  The raw-moment collision in 16-bit storage spills more at 48
-// registers and keeps 4 CTAs (0.772 against 0.817 ms).  General rates: 24
-// warps.
+// registers and keeps 4 CTAs (0.772 against 0.817 ms).  General rates: 4 CTAs
+// of 8 rows (64 registers, a few bytes of spill): on the 512-case batch with
+// every rate equal, -10.6 % in FP32 and -8.6 % in FP16 storage against 3 CTAs
+// at 80 registers.  AXILBM_GENERAL_CTAS overrides the count when building for
+// tuning.
+#ifndef AXILBM_GENERAL_CTAS
+#define AXILBM_GENERAL_CTAS 4
+#endif
 template <class Codec, int BZ, int RM>
 constexpr int step_min_blocks() {
     constexpr int bz8 = (RM == kRatesPaperRaw && sizeof(typename Codec::PT) == 2) ? 4 : 5;
     return sizeof(typename Codec::Real) == 8 ? 1
            : RM != kRatesGeneral ? (BZ >= 16 ? 2 : (BZ >= 8 ? bz8 : 8))
-                : (BZ >= 16 ? 1 : (BZ >= 8 ? 3 : 6));
+                : (BZ >= 16 ? 1 : (BZ >= 8 ? AXILBM_GENERAL_CTAS : 2 * AXILBM_GENERAL_CTAS));
 }
 
 // Store one post-collision population pair (f_i, g_i) in the slot `dst` of
@@ -595,19 +601,17 @@ fields_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ til
     out[4 * n + o] = (double)m.p;
 }
 
-// Initial condition from phi0 (dense [nz][nr] FP64): f = f^eq(phi0, u = 0) of
-// Eq. 11, g = 0, chi^{-1} = (0, M phi0), p^{-1} = 0.  Writes the "in" buffers.
+// Initial condition of node (k, j) of case C from its phi0 (Eq. 11): f =
+// f^eq(phi0, u = 0), g = 0, chi^{-1} = (0, M phi0), p^{-1} = 0, written to the
+// "in" buffers.
 template <class Codec>
-__global__ void init_kernel(CaseDev C, const double* __restrict__ phi0, StateDev<Codec> S) {
+__device__ __forceinline__ void init_node(const CaseDev& C, const StateDev<Codec>& S, int k, int j, double phi0) {
     using Real = typename Codec::Real;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k = blockIdx.y;
-    if (j >= C.nr || k >= C.nz) return;
     const CaseView<Codec> V = case_view<Codec>(S, C);
     const int loc = k * C.pitch + j;
     const Node<Codec> n = V.in_node(loc);
     const CaseReal<Real>& P = case_params<Real>(C);
-    const Real phi = (Real)phi0[(int64_t)k * C.nr + j];
+    const Real phi = (Real)phi0;
     const Real r = (Real)j + (Real)0.5;
     Real fe[9];
     FF ledger{0.0f, 0.0f};
@@ -634,6 +638,22 @@ __global__ void init_kernel(CaseDev C, const double* __restrict__ phi0, StateDev
     n.chz() = (Real)0;
     n.chr() = P.mob * phi;
     n.p() = (Real)0;
+}
+
+// Initial condition of the cases of a tile list, one CTA per 8-row tile:
+// node (k, j) of case c takes phi0[dense_off(c) - base + k nr + j], so one
+// array may hold every case's dense [nz][nr] phi0 in case order (base 0), or
+// one case's alone (base = that case's dense_off).
+template <class Codec>
+__global__ void __launch_bounds__(kTR * 8) init_kernel(const CaseDev* __restrict__ cases,
+                                                       const TileDev* __restrict__ tiles,
+                                                       const double* __restrict__ phi0, int64_t base,
+                                                       StateDev<Codec> S) {
+    const TileDev t = tiles[blockIdx.x];
+    const CaseDev& C = cases[t.c];
+    const int j = t.j0 + threadIdx.x, k = t.k0 + threadIdx.y;
+    if (j >= C.nr || k >= C.nz) return;
+    init_node<Codec>(C, S, k, j, phi0[C.dense_off - base + (int64_t)k * C.nr + j]);
 }
 
 // Decode the state of one case into FP64 arrays (f[9], g[9], aux[3], each [nz][nr]).
@@ -801,10 +821,11 @@ cudaError_t launch_fields_t(const DeviceState& D, int parity, const TileDev* til
 }
 
 template <class Codec>
-cudaError_t launch_init_t(const DeviceState& D, int parity, const CaseDev& C, const double* phi0, cudaStream_t st) {
+cudaError_t launch_init_t(const DeviceState& D, int parity, const TileDev* tiles8, int ntiles, const double* phi0,
+                          int64_t base, cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
     StateDev<Codec> S = make_state<Codec>(D, parity);
-    dim3 grid((C.nr + 127) / 128, C.nz);
-    init_kernel<Codec><<<grid, 128, 0, st>>>(C, phi0, S);
+    init_kernel<Codec><<<ntiles, dim3(kTR, 8), 0, st>>>((const CaseDev*)D.cases, tiles8, phi0, base, S);
     return cudaGetLastError();
 }
 
@@ -838,9 +859,9 @@ cudaError_t launch_set_state_t(const DeviceState& D, int parity, const CaseDev& 
                                      double* out, cudaStream_t st) {                                             \
         return launch_fields_t<CODEC>(D, parity, tiles, ntiles, out, st);                                        \
     }                                                                                                            \
-    cudaError_t launch_init_##NAME(const DeviceState& D, int parity, const CaseDev& C, const double* phi0,       \
-                                   cudaStream_t st) {                                                            \
-        return launch_init_t<CODEC>(D, parity, C, phi0, st);                                                     \
+    cudaError_t launch_init_##NAME(const DeviceState& D, int parity, const TileDev* tiles8, int ntiles,          \
+                                   const double* phi0, int64_t base, cudaStream_t st) {                          \
+        return launch_init_t<CODEC>(D, parity, tiles8, ntiles, phi0, base, st);                                  \
     }                                                                                                            \
     cudaError_t launch_get_state_##NAME(const DeviceState& D, int parity, const CaseDev& C, double* f,           \
                                         double* g, double* aux, cudaStream_t st) {                               \
