@@ -1,0 +1,83 @@
+"""The benchmark's full workload in the launch configuration bench.py times
+(needs a GB300): 512 batched cases, 27.5 M nodes, the launch shape chosen by
+lbm_autotune.
+
+* Properties at full size: the mass (sum r phi) of every one of the 512
+  cases is conserved to the ledger's round-off, and every case stays finite.
+* Sampled outputs the oracle can compute one by one: four cases of the batch
+  (one per density ratio and the largest) against the FP64 oracle run alone,
+  within the FP32 bounds of test_gpu_configs.py; and against the same case
+  run alone on the GPU, bit for bit (a case's result does not depend on the
+  batch around it).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_09299_gb300 import lbm, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 20
+
+
+@pytest.fixture(scope="module", params=["fp32", "mix_fp16"])
+def batch(request):
+    prec = request.param
+    cases = W.batched_cases(512, seed=20181022, precision=prec)
+    sim = lbm.Simulation(cases)
+    phi_all = np.concatenate([W.initial_phi(c).ravel() for c in cases])
+    sim.init_all(np.ascontiguousarray(phi_all))
+    mass0 = [sim.diagnostics(i)["mass"] for i in range(len(cases))]
+    variant = sim.autotune(reps=2)
+    sim.step(STEPS)
+    yield prec, cases, sim, mass0, variant
+    sim.close()
+
+
+def _sampled(cases):
+    picked, seen = [], set()
+    for i, c in enumerate(cases):
+        ratio = round(c["rho_l"] / c["rho_g"])
+        if ratio not in seen:
+            seen.add(ratio)
+            picked.append(i)
+    picked.append(int(np.argmax([c["nr"] * c["nz"] for c in cases])))
+    return picked
+
+
+def test_every_case_conserves_mass(batch):
+    prec, cases, sim, mass0, _ = batch
+    assert sum(c["nr"] * c["nz"] for c in cases) == 27476224
+    worst = 0.0
+    for i in range(len(cases)):
+        d = sim.diagnostics(i)
+        assert d["nonfinite"] == 0 and d["step"] == STEPS, (i, d)
+        worst = max(worst, abs(d["mass"] - mass0[i]) / mass0[i])
+    assert worst < 1e-8, worst
+
+
+def test_sampled_cases_against_the_oracle(batch):
+    prec, cases, sim, _, _ = batch
+    bound = {"fp32": (1e-2, 5e-4), "mix_fp16": (4e-2, 1.5e-3)}[prec]
+    for i in _sampled(cases):
+        c = cases[i]
+        ref = oracle.Oracle(dict(c, precision="fp64")).init(W.initial_phi(c)).step(STEPS).fields()
+        got = sim.fields(i)
+        e = got["phi"] - ref["phi"]
+        mx, l2 = float(np.max(np.abs(e))), float(np.sqrt(np.mean(e * e)))
+        print(prec, "case", i, f"{c['nr']}x{c['nz']}", "phi max/L2", mx, l2)
+        assert mx < bound[0] and l2 < bound[1], (i, mx, l2)
+
+
+def test_sampled_cases_equal_single_case_runs(batch):
+    prec, cases, sim, _, variant = batch
+    for i in _sampled(cases)[:2]:
+        one = lbm.Simulation(cases[i])
+        one.set_variant(variant)
+        one.init_phase(0, "host_array", phi=W.initial_phi(cases[i]))
+        one.step(STEPS)
+        a, b = one.fields(0), sim.fields(i)
+        one.close()
+        for k in ("phi", "uz", "ur", "p"):
+            assert np.array_equal(a[k], b[k]), (i, k)
