@@ -368,6 +368,106 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
                                chr_prev, p_prev, kInvrTable ? s_invr : nullptr, kKeepF ? f : nullptr);
 }
 
+// The step with two nodes per thread, one after the other: thread (x, y) of
+// a CTA of BZ warps updates nodes (k0 + y, j0 + x) and (k0 + y + BZ, j0 + x)
+// of a tile of 2 BZ rows with the one-node update of node_update, so the
+// results are those of step_kernel.  Both nodes' loads are in flight before
+// the tile's barrier (twice the loads per thread), and the phi ring is shared
+// by twice the nodes.
+#ifndef AXILBM_SEQ2_CTAS
+#define AXILBM_SEQ2_CTAS 3
+#endif
+template <class Codec, int BZ, int RM>
+constexpr int seq2_min_blocks() {
+    return sizeof(typename Codec::Real) == 8 ? 1 : (BZ >= 8 ? AXILBM_SEQ2_CTAS : 2 * AXILBM_SEQ2_CTAS);
+}
+
+template <class Codec, int BZ, int RM>
+__global__ void __launch_bounds__(kTR * BZ, (seq2_min_blocks<Codec, BZ, RM>()))
+step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles, StateDev<Codec> S,
+                 const CUtensorMap* __restrict__ maps, int map_set, int parity, int ntiles, int ahead) {
+    using Real = typename Codec::Real;
+    using PT = typename Codec::PT;
+    using F0T = typename Codec::F0T;
+    constexpr int TZ = 2 * BZ;
+    constexpr int LD = kTR + 4;
+    constexpr int NRING = 4 * kTR + 4 * (TZ + 4);
+    static_assert(NRING == (TZ + 4) * LD - TZ * kTR, "the ring is the window without the tile");
+    static_assert(sizeof(Real) == 4, "FP32 arithmetic");
+    __shared__ Real sphi[(TZ + 4) * LD];
+    __shared__ __align__(16) CaseDev sC;
+    static_assert(sizeof(CaseDev) % 4 == 0 && sizeof(CaseDev) / 4 <= kTR * BZ, "one word per thread");
+    const TileDev t = tiles[blockIdx.x];
+    if (maps != nullptr && threadIdx.x == 0 && threadIdx.y == 0 && (int)blockIdx.x + ahead < ntiles) {
+        const TileDev tp = tiles[blockIdx.x + ahead];
+        const CUtensorMap* M = maps + ((size_t)tp.c * 2 + map_set) * kMapsPerCase + 2 + parity;
+        tensormap_acquire(M);
+        tma_prefetch_4d(M, 0, 0, tp.j0 >> 5, tp.k0);
+    }
+    {
+        const int q = threadIdx.y * kTR + threadIdx.x;
+        if (q < (int)(sizeof(CaseDev) / 4))
+            reinterpret_cast<int32_t*>(&sC)[q] = reinterpret_cast<const int32_t*>(cases + t.c)[q];
+    }
+    __syncthreads();
+    const CaseDev& C = sC;
+    const CaseView<Codec> V = case_view<Codec>(S, C);
+    const int j = t.j0 + threadIdx.x;
+    // 1. both nodes' own loads, issued before anything waits on memory
+    F0T f0raw[2] = {};
+    PT fraw[2][8], graw[2][9];
+    Real chz_prev[2] = {}, chr_prev[2] = {}, p_prev[2] = {};
+    bool in[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int k = t.k0 + threadIdx.y + p * BZ;
+        in[p] = (j < C.nr) && (k < C.nz);
+        if (in[p]) {
+            const Node<Codec> n = V.in_node(k * C.pitch + j);
+            f0raw[p] = n.f0();
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const typename Codec::PT2 pr = n.pair(i);
+                fraw[p][i - 1] = pr.x;
+                graw[p][i] = pr.y;
+            }
+            graw[p][0] = n.g(0);
+            chz_prev[p] = n.chz();
+            chr_prev[p] = n.chr();
+            if (C.p_coupling == 1) p_prev[p] = n.p();
+        }
+    }
+    // 2. the ring of the phi window
+    for (int q = threadIdx.y * kTR + threadIdx.x; q < NRING; q += kTR * BZ) {
+        int a, b;
+        ring_cell<TZ>(q, a, b);
+        sphi[a * LD + b] = window_phi<Codec>(C, V, t, a, b);
+    }
+    // 3. both nodes' own phi (Eq. 16), in the form of the one-node kernel
+    const Real r = (Real)j + (Real)0.5;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int a = threadIdx.y + 2 + p * BZ;
+        if (in[p]) {
+            Real sum = (Real)f0_value(f0raw[p]);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) sum += Codec::dec_f(fraw[p][i - 1], (Real)w_of(i) * r);
+            sphi[a * LD + threadIdx.x + 2] =
+                sizeof(PT) == 2 ? phi_of<Codec>(f0raw[p], fraw[p], rcp_(r)) : sum * rcp_(r);
+        } else {
+            sphi[a * LD + threadIdx.x + 2] = window_phi<Codec>(C, V, t, a, threadIdx.x + 2);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        if (!in[p]) continue;
+        const int k = t.k0 + threadIdx.y + p * BZ;
+        node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2 + p * BZ, threadIdx.x + 2, k, j, k * C.pitch + j,
+                                   f0raw[p], fraw[p], graw[p], chz_prev[p], chr_prev[p], p_prev[p]);
+    }
+}
+
 // Shared-memory layout of one stage of the TMA-pipelined step for tile
 // height TZ, then the phi window and one mbarrier per stage.  A stage holds
 // its tile's record, the record of the tile after it in the CTA's walk, the
@@ -794,7 +894,23 @@ void launch_step_rates(int variant, int ntiles, cudaStream_t st, const CaseDev* 
                 cs, tiles, S, maps, 0, parity, ntiles, kPrefetchQuarters * sms * step_min_blocks<Codec, 4, RM>() / 4);
             break;
         case 3: launch_tma<Codec, 8, RM>(ntiles, st, cs, tiles, S, D, parity); break;
-        default: launch_tma<Codec, 16, RM>(ntiles, st, cs, tiles, S, D, parity); break;
+        case 4: launch_tma<Codec, 16, RM>(ntiles, st, cs, tiles, S, D, parity); break;
+        case 5:
+            if constexpr (sizeof(typename Codec::Real) == 4)
+                step_kernel_seq2<Codec, 8, RM><<<ntiles, dim3(kTR, 8), 0, st>>>(
+                    cs, tiles, S, maps, 1, parity, ntiles, kPrefetchQuarters * sms * seq2_min_blocks<Codec, 8, RM>() / 4);
+            else
+                step_kernel<Codec, 16, RM><<<ntiles, dim3(kTR, 16), 0, st>>>(
+                    cs, tiles, S, maps, 1, parity, ntiles, kPrefetchQuarters * sms * step_min_blocks<Codec, 16, RM>() / 4);
+            break;
+        default:
+            if constexpr (sizeof(typename Codec::Real) == 4)
+                step_kernel_seq2<Codec, 4, RM><<<ntiles, dim3(kTR, 4), 0, st>>>(
+                    cs, tiles, S, maps, 0, parity, ntiles, kPrefetchQuarters * sms * seq2_min_blocks<Codec, 4, RM>() / 4);
+            else
+                step_kernel<Codec, 8, RM><<<ntiles, dim3(kTR, 8), 0, st>>>(
+                    cs, tiles, S, maps, 0, parity, ntiles, kPrefetchQuarters * sms * step_min_blocks<Codec, 8, RM>() / 4);
+            break;
     }
 }
 
