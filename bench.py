@@ -42,10 +42,10 @@ BYTES_PER_NODE = {
     "mix_fp16": 2 * (8 + 8 * 2 + 9 * 2 + 2 * 4),  # 100
     "mix_bf16": 2 * (8 + 8 * 2 + 9 * 2 + 2 * 4),  # 100
 }
-# The survey's per-node byte count (populations f and g read and written, phi
-# once each way, chi^{n-1} and p^{n-1} read and written), reported beside the
-# narrower count above.
-BYTES_PER_NODE_SURVEY = {"fp64": 352, "fp32": 176, "mix_fp16": 108, "mix_bf16": 108}
+# The wider per-node byte count that also charges the p^{n-1} plane (read and
+# written) and phi once each way: populations f and g read and written, the
+# f_0 ledger, chi^{n-1} and p^{n-1}; reported beside the count above.
+BYTES_PER_NODE_WITH_P = {"fp64": 352, "fp32": 176, "mix_fp16": 108, "mix_bf16": 108}
 DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf16": "f32 (bf16 storage)"}
 # DRAM bytes per node update of the step kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the nodes of the captured
@@ -328,7 +328,7 @@ def run_cuda(args):
     peak, peak_kind = measured_peaks()
     per_launch_ms = float(np.mean(times))
     achieved = BYTES_PER_NODE[prec] * nodes / (per_launch_ms * 1e-3) / 1e9
-    ach_survey = BYTES_PER_NODE_SURVEY[prec] * nodes / (per_launch_ms * 1e-3) / 1e9
+    ach_with_p = BYTES_PER_NODE_WITH_P[prec] * nodes / (per_launch_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -349,8 +349,8 @@ def run_cuda(args):
                      "traffic_unit": "bytes per launch (ncu capture of 64 cases scaled by node count)",
                      "note": f"peak {peak_kind}; algorithmic bytes {BYTES_PER_NODE[prec]} B/node x {nodes} nodes "
                              f"per launch / mean CUDA-event launch duration",
-                     "survey_bytes_per_node": BYTES_PER_NODE_SURVEY[prec], "achieved_survey": ach_survey,
-                     "frac_survey": ach_survey / peak},
+                     "bytes_per_node_with_p": BYTES_PER_NODE_WITH_P[prec], "achieved_with_p": ach_with_p,
+                     "frac_with_p": ach_with_p / peak},
         "gpu_launches": int(launches),
         # the autotuner restores the state it started from, so d["step"] counts
         # the warm-up and timed steps only
@@ -505,10 +505,12 @@ def batched_other(torch, args, prec, steps, raw=False):
     peak, kind = measured_peaks()
     ach = BYTES_PER_NODE[prec] * nodes / (ms * 1e-3) / 1e9
     sim.close()
+    ach_p = BYTES_PER_NODE_WITH_P[prec] * nodes / (ms * 1e-3) / 1e9
     out = {"precision": prec, "collision": "raw moments" if raw else "orthogonal (paper)",
            "value": nodes / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
            "variant": variant, "achieved_gbs": ach, "frac": ach / peak,
-           "bytes_per_node": BYTES_PER_NODE[prec]}
+           "bytes_per_node": BYTES_PER_NODE[prec], "frac_with_p": ach_p / peak,
+           "bytes_per_node_with_p": BYTES_PER_NODE_WITH_P[prec]}
     if prec == "fp64":
         gops = FP64_OPS_PER_NODE * nodes / (ms * 1e-3) / 1e9
         with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
