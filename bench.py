@@ -49,10 +49,11 @@ BYTES_PER_NODE_WITH_P = {"fp64": 352, "fp32": 176, "mix_fp16": 108, "mix_bf16": 
 DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf16": "f32 (bf16 storage)"}
 # DRAM bytes per node update of the step kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the nodes of the captured
-# launch; profiles/step_kernel_fp32_batched64cases.md), keyed by precision,
-# launch variant and collision basis.  Scaled to a full launch by the node count.  Kept only for
-# the kernel build that was captured.
-TRAFFIC_B_PER_NODE = {("fp32", 0, "orthogonal"): 164.96}
+# launch), keyed by precision, launch variant and collision basis:
+# profiles/step_kernel_fp32_batched64cases.md (variant 0) and
+# profiles/step_kernel_seq2_fp32_batched64cases.md (variant 5).  Scaled to a
+# full launch by the node count.  Kept only for the kernel builds captured.
+TRAFFIC_B_PER_NODE = {("fp32", 0, "orthogonal"): 164.96, ("fp32", 5, "orthogonal"): 164.1}
 # The FP64 step is bound by the FP64 pipe, not by HBM: FP64-pipe thread
 # instructions (DADD + DFMA + DMUL) per node update from one ncu capture
 # (profiles/step_kernel_fp64_batched64cases.md), against the pipe's rate
