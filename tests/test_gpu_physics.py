@@ -63,7 +63,7 @@ def _fit_frequency(ts, L, w0):
     return abs(popt[3])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "mix_fp16"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mix_fp16", "mix_bf16"])
 def test_oscillating_drop_frequency(prec):
     """128 x 256 P2 drop (R0 = 32, eps = 0.05, ratio 100, sigma = 0.005), 20,000
     steps: the n = 2 frequency of the axis half-length within 10 % of Eq. 43."""
@@ -87,7 +87,7 @@ def _axis_neck(sim):
     return float(phi[:, 0].min())
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mix_fp16"])
+@pytest.mark.parametrize("prec", ["fp64", "mix_fp16", "mix_bf16"])
 def test_thread_breaks_up_below_rayleigh_limit(prec):
     """Periodic thread R0 = 20, k = 2 pi R0 / lambda = 0.7 < 1, ratio 1000: the
     neck on the axis pinches off (phi < 1/2) within 30,000 steps."""
