@@ -288,7 +288,14 @@ int lbm_checkpoint_load(lbm_handle* h, const void* host_buf);
  * *chosen (may be NULL).  Synchronises. */
 int lbm_autotune(lbm_handle* h, int32_t reps, int32_t* chosen);
 
-/* Select a step-kernel launch variant explicitly (0 .. lbm_num_variants()-1). */
+/* Select a step-kernel launch variant explicitly (0 .. lbm_num_variants()-1).
+ * Every variant computes bit-identical results; they differ in tile height
+ * (rows along z of the 32-column tile), in nodes per thread and in staging:
+ *   0, 1, 2  one node per thread, tiles of 8, 16, 4 rows;
+ *   3, 4     one node per thread, tiles of 8, 16 rows staged in shared memory
+ *            by TMA copies (persistent, pipelined; needs the tensor maps);
+ *   5, 6     two nodes of a column per thread, tiles of 16 and 8 rows
+ *            (FP64 handles run the one-node kernel of the same tile height). */
 int lbm_set_variant(lbm_handle* h, int32_t variant);
 int32_t lbm_num_variants(void);
 
