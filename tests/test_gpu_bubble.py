@@ -1,0 +1,77 @@
+"""The rising bubble against the FP64 oracle (needs a GB300).
+
+The benchmark's fourth configuration asks for the bubble's terminal velocity
+and shape against the FP64 oracle.  The paper's bubble section is absent, so
+the reference is the oracle itself, run for the same steps: the rise velocity
+(a line fit of the bubble's midpoint on the axis over the terminal stretch of
+the rise) and the bubble's height and width, in every storage precision.  The
+full-size case (256 x 1024, R = 32) is run against the oracle once, with the
+numbers in the design notes; this test runs the same physics on a 64 x 256
+grid (R = 12, Eo = 10, density ratio 1000, M = 0.05) whose oracle run takes
+seconds.  The bubble rises at a steady 0.046 per step between steps 2000 and
+4000 and reaches the top wall near step 4500.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_09299_gb300 import lbm, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+EVERY, STEPS, FIT_FROM = 250, 4000, 2000
+
+
+def _bubble(phi):
+    """(bottom, top) of the phi < 1/2 run on the axis row (interpolated
+    crossings) and the half-width on the row of its midpoint."""
+    ax = phi[:, 0]
+    ks = np.where(ax < 0.5)[0]
+    k0, k1 = ks.min(), ks.max()
+    zb = (k0 - 0.5) + (ax[k0 - 1] - 0.5) / (ax[k0 - 1] - ax[k0])
+    zt = (k1 + 0.5) + (0.5 - ax[k1]) / (ax[k1 + 1] - ax[k1])
+    row = phi[int(0.5 * (zb + zt))]
+    j1 = np.where(row >= 0.5)[0].min()
+    rw = (j1 - 0.5) + (0.5 - row[j1 - 1]) / (row[j1] - row[j1 - 1])
+    return zb, zt, rw
+
+
+def _track(step, fields):
+    out = []
+    for _ in range(STEPS // EVERY):
+        step(EVERY)
+        out.append(_bubble(fields()["phi"]))
+    steps = np.arange(1, len(out) + 1) * EVERY
+    mid = np.array([0.5 * (a + b) for a, b, _ in out])
+    sel = steps > FIT_FROM
+    v = float(np.polyfit(steps[sel], mid[sel], 1)[0])
+    zb, zt, rw = out[-1]
+    return v, zt - zb, rw
+
+
+@pytest.fixture(scope="module")
+def reference():
+    case = W.rising_bubble(nr=64, nz=256, R=12.0, zc=48.0, precision="fp64")
+    o = oracle.Oracle(case).init(W.initial_phi(case))
+    return case, _track(lambda n: o.step(n), o.fields)
+
+
+# Relative bounds on the rise velocity and on the bubble's height and
+# half-width against the oracle's.
+BOUND_V = {"fp64": 1e-4, "fp32": 1e-3, "mix_fp16": 1e-2, "mix_bf16": 0.1}
+BOUND_SHAPE = {"fp64": 1e-4, "fp32": 2e-3, "mix_fp16": 2e-2, "mix_bf16": 0.1}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mix_fp16", "mix_bf16"])
+def test_rise_velocity_and_shape_follow_the_oracle(reference, prec):
+    case, (v_ref, h_ref, w_ref) = reference
+    sim = lbm.Simulation(dict(case, precision=prec))
+    sim.init_case(0)
+    v, h, w = _track(lambda n: sim.step(n), lambda: sim.fields(which=("phi",)))
+    assert sim.diagnostics()["nonfinite"] == 0
+    sim.close()
+    print(prec, "rise velocity", v, "oracle", v_ref, "height", h, h_ref, "half-width", w, w_ref)
+    assert 0.04 < v_ref < 0.05
+    assert abs(v - v_ref) <= BOUND_V[prec] * v_ref, (v, v_ref)
+    assert abs(h - h_ref) <= BOUND_SHAPE[prec] * h_ref, (h, h_ref)
+    assert abs(w - w_ref) <= BOUND_SHAPE[prec] * w_ref, (w, w_ref)
