@@ -49,29 +49,49 @@ def _track(step, fields):
     return v, zt - zb, rw
 
 
+def _oracle_run(case, phi0):
+    o = oracle.Oracle(case).init(phi0)
+    return np.array(_track(lambda n: o.step(n), o.fields))
+
+
 @pytest.fixture(scope="module")
 def reference():
+    """The oracle's rise velocity, height and half-width, and how far they
+    move when one node of phi0 changes by 1e-15: the FP64 round-off horizon
+    of a rising liquid where phi overshoots 1 (the micro-state of two FP64
+    runs separates within a few hundred steps; the bubble's motion moves by
+    3e-4 of the velocity and 8e-4 of the width over 4000 steps)."""
     case = W.rising_bubble(nr=64, nz=256, R=12.0, zc=48.0, precision="fp64")
-    o = oracle.Oracle(case).init(W.initial_phi(case))
-    return case, _track(lambda n: o.step(n), o.fields)
+    phi0 = W.initial_phi(case)
+    ref = _oracle_run(case, phi0)
+    nudged = phi0.copy()
+    nudged[100, 5] += 1e-15
+    spread = np.abs(_oracle_run(case, nudged) - ref) / ref
+    return case, ref, spread
 
 
 # Relative bounds on the rise velocity and on the bubble's height and
-# half-width against the oracle's.
-BOUND_V = {"fp64": 1e-4, "fp32": 1e-3, "mix_fp16": 1e-2, "mix_bf16": 0.1}
-BOUND_SHAPE = {"fp64": 1e-4, "fp32": 2e-3, "mix_fp16": 2e-2, "mix_bf16": 0.1}
+# half-width against the oracle's.  FP64 is held to three times the oracle's
+# own spread under a 1e-15 nudge of phi0 (round-off decides the rest).
+BOUND_V = {"fp32": 1e-3, "mix_fp16": 1e-2, "mix_bf16": 0.1}
+BOUND_SHAPE = {"fp32": 2e-3, "mix_fp16": 2e-2, "mix_bf16": 0.1}
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "mix_fp16", "mix_bf16"])
 def test_rise_velocity_and_shape_follow_the_oracle(reference, prec):
-    case, (v_ref, h_ref, w_ref) = reference
+    case, (v_ref, h_ref, w_ref), spread = reference
     sim = lbm.Simulation(dict(case, precision=prec))
     sim.init_case(0)
     v, h, w = _track(lambda n: sim.step(n), lambda: sim.fields(which=("phi",)))
     assert sim.diagnostics()["nonfinite"] == 0
     sim.close()
-    print(prec, "rise velocity", v, "oracle", v_ref, "height", h, h_ref, "half-width", w, w_ref)
+    print(prec, "rise velocity", v, "oracle", v_ref, "height", h, h_ref, "half-width", w, w_ref,
+          "oracle spread", spread)
     assert 0.04 < v_ref < 0.05
-    assert abs(v - v_ref) <= BOUND_V[prec] * v_ref, (v, v_ref)
-    assert abs(h - h_ref) <= BOUND_SHAPE[prec] * h_ref, (h, h_ref)
-    assert abs(w - w_ref) <= BOUND_SHAPE[prec] * w_ref, (w, w_ref)
+    if prec == "fp64":
+        bv, bh, bw = np.maximum(3.0 * spread, 1e-9)
+    else:
+        bv, bh, bw = BOUND_V[prec], BOUND_SHAPE[prec], BOUND_SHAPE[prec]
+    assert abs(v - v_ref) <= bv * v_ref, (v, v_ref, bv)
+    assert abs(h - h_ref) <= bh * h_ref, (h, h_ref, bh)
+    assert abs(w - w_ref) <= bw * w_ref, (w, w_ref, bw)
