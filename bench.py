@@ -34,18 +34,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS and % HBM roofline: FP64/FP32 vs mixed-precision/batched at stated error"
-# Algorithmic bytes per node update (populations read + written, f_0 ledger in
-# FP64, chi^{n-1} read + written; the lagged-p array is not touched).
+# Algorithmic bytes per node update (populations read + written, f_0 -- FP64,
+# the FP32 ledger pair, or the 16-bit forms' single FP32 ledger value --,
+# chi^{n-1} read + written; the lagged-p array is not touched).
 BYTES_PER_NODE = {
     "fp64": 2 * (9 * 8 + 9 * 8 + 2 * 8),       # 320
     "fp32": 2 * (8 + 8 * 4 + 9 * 4 + 2 * 4),    # 168
-    "mix_fp16": 2 * (8 + 8 * 2 + 9 * 2 + 2 * 4),  # 100
-    "mix_bf16": 2 * (8 + 8 * 2 + 9 * 2 + 2 * 4),  # 100
+    "mix_fp16": 2 * (4 + 8 * 2 + 9 * 2 + 2 * 4),  # 92
+    "mix_bf16": 2 * (4 + 8 * 2 + 9 * 2 + 2 * 4),  # 92
 }
 # The wider per-node byte count that also charges the p^{n-1} plane (read and
-# written) and phi once each way: populations f and g read and written, the
-# f_0 ledger, chi^{n-1} and p^{n-1}; reported beside the count above.
-BYTES_PER_NODE_WITH_P = {"fp64": 352, "fp32": 176, "mix_fp16": 108, "mix_bf16": 108}
+# written; FP64 also phi once each way); reported beside the count above.
+BYTES_PER_NODE_WITH_P = {"fp64": 352, "fp32": 176, "mix_fp16": 100, "mix_bf16": 100}
 DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf16": "f32 (bf16 storage)"}
 # DRAM bytes per node update of the step kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the nodes of the captured
@@ -106,6 +106,13 @@ class ClockSampler:
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
                  "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
+            # nvidia-smi takes a few hundred ms to print its first sample: wait
+            # for it so that the samples cover the whole timed region
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
@@ -548,7 +555,7 @@ def single_case(torch, workload, prec, steps):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--workload", default="batched", choices=["batched", "oscillating", "static"])

@@ -49,15 +49,22 @@ typedef enum {
 /* Storage and arithmetic precision of a handle.
  *   LBM_FP64      populations and arithmetic in FP64.
  *   LBM_FP32      populations f_1..8 and g_0..8 in FP32, arithmetic in FP32.
+ *                 f_0 is stored as a pair of FP32 numbers holding the node's
+ *                 mass ledger: (sum of its incoming populations) minus (its
+ *                 stored outgoing f_1..8), accumulated with error-free FP32
+ *                 additions, so the sum of all populations (the conserved sum
+ *                 of r phi, Eq. 16) changes only by round-off of about 2^-48.
  *   LBM_MIX_FP16  populations f_1..8 and g_0..8 stored as FP16 deviations
- *                 (f_i / (w_i r) - 1/2 and 256 g_i / (w_i r), r of the storing
- *                 node); arithmetic in FP32; reductions in FP64.
- *   LBM_MIX_BF16  as LBM_MIX_FP16 with bfloat16 storage (no g scale).
- * In the FP32 and 16-bit forms f_0 is stored as a pair of FP32 numbers holding
- * the node's mass ledger: (sum of its incoming populations) minus (its stored
- * outgoing f_1..8), accumulated with error-free FP32 additions, so the sum of
- * all populations (the conserved sum of r phi, Eq. 16) changes only by round-off
- * of about 2^-48. */
+ *                 f_i / S_i - 1/2 and 256 g_i / S_i, S_i = w_i r of the
+ *                 storing node rounded up to 2 significant bits (FP16; 7 for
+ *                 bfloat16) in the ratios of the weights, the f deviation on a
+ *                 2^-14 grid (2^-9 for bfloat16); arithmetic in FP32;
+ *                 reductions in FP64.  Every stored f_i then decodes exactly,
+ *                 to a multiple of a per-column grid, so f_0, one FP32 number,
+ *                 holds the node's mass ledger in exact FP32 arithmetic: the
+ *                 step conserves the sum of all populations exactly.
+ *                 nr <= 65536.
+ *   LBM_MIX_BF16  as LBM_MIX_FP16 with bfloat16 storage (no g scale). */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_MIX_FP16 = 2, LBM_MIX_BF16 = 3 } lbm_precision;
 
 /* Coupling of the pressure p and the radial velocity u_r (Eq. 32 uses p, Eq. 33

@@ -22,9 +22,11 @@ using namespace axilbm;
 namespace {
 
 constexpr int kGraphSteps = 32;  // steps per captured graph (even: parity returns)
+constexpr int kMax16BitNr = 65536;  // largest nr of the 16-bit storage forms
 
 size_t pt_size(int prec) { return prec == LBM_FP64 ? 8 : (prec == LBM_FP32 ? 4 : 2); }
-size_t f0_size(int) { return 8; }  // f_0 is 8 bytes in every precision (FP64, or the FP32 ledger pair)
+// f_0: FP64, the FP32 ledger pair, or the 16-bit forms' one FP32 ledger value
+size_t f0_size(int prec) { return prec == LBM_MIX_FP16 || prec == LBM_MIX_BF16 ? 4 : 8; }
 size_t real_size(int prec) { return prec == LBM_FP64 ? 8 : 4; }
 // bytes of one storage block (32 nodes) in this precision
 size_t block_bytes(int prec) {
@@ -42,6 +44,9 @@ int validate(const lbm_params& p) {
         return LBM_ERR_INVALID_ARG;
     if (p.z_periodic != 0 && p.z_periodic != 1) return LBM_ERR_INVALID_ARG;
     if (p.precision < LBM_FP64 || p.precision > LBM_MIX_BF16) return LBM_ERR_INVALID_ARG;
+    // 16-bit storage: the column scales P / 8 (P <= 2 nr) are FP16 numbers
+    if ((p.precision == LBM_MIX_FP16 || p.precision == LBM_MIX_BF16) && p.nr > kMax16BitNr)
+        return LBM_ERR_INVALID_ARG;
     if (p.p_coupling != LBM_P_EXACT && p.p_coupling != LBM_P_LAGGED) return LBM_ERR_INVALID_ARG;
     if (p.collision != LBM_MRT_ORTHOGONAL && p.collision != LBM_MRT_RAW) return LBM_ERR_INVALID_ARG;
     if (!finite_pos(p.rho_l) || !finite_pos(p.rho_g) || !finite_pos(p.nu_l) || !finite_pos(p.nu_g))

@@ -116,6 +116,7 @@ struct CodecF64 {
     using PT = double;
     using F0T = double;
     static constexpr bool kLedger = false;
+    static constexpr bool kGrid = false;
     static constexpr bool kStreamStores = false;
     using PT2 = double2;  // (f_i, g_i) of one direction, stored together
     __device__ static Real dec_f(PT v, Real) { return v; }
@@ -131,6 +132,7 @@ struct CodecF32 {
     using F0T = float2;
     using PT2 = float2;
     static constexpr bool kLedger = true;
+    static constexpr bool kGrid = false;
     static constexpr bool kStreamStores = false;
     __device__ static Real dec_f(PT v, Real) { return v; }
     __device__ static PT enc_f(Real v, Real, Real) { return v; }
@@ -139,10 +141,10 @@ struct CodecF32 {
     __device__ static PT2 enc_pair(Real f, Real g, Real, Real) { return make_float2(f, g); }
 };
 
-// Mixed-precision adds (PTX ISA 8.6, sm_100 family): the 16-bit operand is
-// converted exactly and added to the FP32 one with one rounding, the same
-// result as a conversion followed by an FP32 add (checked bit for bit over
-// every FP16 value on the GPU), in one instruction.
+// Mixed-precision adds and FMAs (PTX ISA 8.6, sm_100 family): the 16-bit
+// operands are taken exactly and the FP32 result is rounded once, in one
+// instruction (the add checked bit for bit against a conversion followed by
+// an FP32 add over every FP16 value on the GPU).
 __device__ __forceinline__ float add_h(__half h, float c) {
     float d;
     asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(__half_as_ushort(h)), "f"(c));
@@ -153,69 +155,179 @@ __device__ __forceinline__ float add_h(__nv_bfloat16 h, float c) {
     asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(__bfloat16_as_ushort(h)), "f"(c));
     return d;
 }
-
-// phi of a node (Eq. 16) from its raw stored f_0 and f_1..8: sum f_i / r.
-// With the 16-bit decode f_i = (h_i + 1/2) w_i r the sum reads
-//   phi = f_0 / r + (h_1 + .. + h_4 + 2) / 9 + (h_5 + .. + h_8 + 2) / 36,
-// summed from the stored values with eight mixed-precision adds (no decode);
-// every path that forms phi of a 16-bit node uses this one form, so the phi
-// window is the same whichever tile or launch shape computes a cell.
-template <typename PT>
-__device__ __forceinline__ float phi_from_halves(float f0, const PT* h, float inv_r) {
-    float a = 2.0f, b = 2.0f;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) a = add_h(h[i], a);
-#pragma unroll
-    for (int i = 4; i < 8; ++i) b = add_h(h[i], b);
-    return __fmaf_rn(f0, inv_r, __fmaf_rn(a, 1.0f / 9.0f, b * (1.0f / 36.0f)));
+// a * b + c with a, b 16-bit (b given by its bits)
+__device__ __forceinline__ float fma_h(__half a, uint16_t b, float c) {
+    float d;
+    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(__half_as_ushort(a)), "h"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float fma_h(__nv_bfloat16 a, uint16_t b, float c) {
+    float d;
+    asm("fma.rn.f32.bf16 %0, %1, %2, %3;" : "=f"(d) : "h"(__bfloat16_as_ushort(a)), "h"(b), "f"(c));
+    return d;
 }
 
 // kStreamStores: the step writes its pushed populations with evict-first
 // stores (measured: -1.5 % on the 16-bit step, +2.8 % on the FP32 one).
 //
-// 16-bit deviation storage: f_i / (w_i r) - 1/2 (phi-like, centred) and
-// g_i / (w_i r) * scale (rest state g = 0; the scale keeps typical values
-// out of the FP16 subnormal range).  f is decoded as h wr + wr/2 in one
-// explicit FMA (wr/2 is exact), the same expression for the writer's mass
-// ledger and for the next reader, so both round alike; the g scale is folded
-// into the encoder's reciprocal (a power of two, exact).
-struct CodecH16 {
-    using Real = float;
-    using PT = __half;
-    using F0T = float2;
-    using PT2 = __half2;
-    static constexpr bool kLedger = true;
-    static constexpr bool kStreamStores = true;
-    static constexpr float kGScale = 256.0f;
-    __device__ static Real dec_f(PT v, Real wr) { return __fmaf_rn(__half2float(v), wr, 0.5f * wr); }
-    __device__ static PT enc_f(Real v, Real, Real inv_wr) { return __float2half_rn(v * inv_wr - 0.5f); }
-    __device__ static Real dec_g(PT v, Real wr) { return __half2float(v) * (wr * (1.0f / kGScale)); }
-    __device__ static PT enc_g(Real v, Real, Real inv_wr) { return __float2half_rn(v * (inv_wr * kGScale)); }
-    // both values of a direction in one packed conversion
-    __device__ static PT2 enc_pair(Real f, Real g, Real, Real inv_wr) {
-        return __floats2half2_rn(f * inv_wr - 0.5f, g * (inv_wr * kGScale));
-    }
+// 16-bit storage on a grid.  Column j (r = j + 1/2) has the scales S_i of its
+// directions: S_a = w_1 r = r / 9 rounded up to kScaleBits significant bits,
+// S_i = S_a for i = 1..4, S_a / 4 for i = 5..8, 4 S_a for i = 0 (the weights'
+// ratios), so S_i = w_i r / alpha with alpha in (2/3, 1] (FP16: 2 bits) or
+// (0.98, 1] (bfloat16: 7 bits).  f_i (i = 1..8) is stored as the centred
+// deviation
+//   h_i = f_i / S_i - 1/2,
+// first rounded to a multiple of 2^-kGridExp, then to the 16-bit format
+// (which keeps it on that grid), and decoded as
+//   f_i = (h_i + 1/2) S_i   (one mixed-precision FMA),
+// which is exact: a number of kGridExp + 1 bits times one of kScaleBits bits,
+// kGridExp + kScaleBits <= 16.  f_i = 0 (the phase phi = 0) is stored as
+// exactly -1/2.  Every value a node's mass ledger adds or subtracts (its
+// incoming f_1..8 decoded at its own column, the f_1..8 it stores decoded at
+// the destination columns j-1, j, j+1, and its own f_0) is then a multiple of
+// q = 2^-kGridExp ulp(S_5 of column max(j - 1, 0)), ulp at kScaleBits bits,
+// and every partial sum (at most about r phi) stays below 2^24 q for phi up to
+// about 2, so plain FP32 additions of them are exact: f_0 is one FP32 value,
+// (sum of the incoming populations) minus (the stored outgoing f_1..8), and the
+// step conserves the sum of all populations exactly.
+// g_i is stored as kGScale g_i / S_i (FP16: the scale keeps typical values out
+// of the subnormal range; bfloat16 has FP32's range and takes no scale).
+__device__ __forceinline__ uint16_t bits16(__half v) { return __half_as_ushort(v); }
+__device__ __forceinline__ uint16_t bits16(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
+template <typename PT>
+__device__ __forceinline__ PT to16(float v);
+template <>
+__device__ __forceinline__ __half to16<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// The constants of one column (see above).  Axis class (directions 1..4),
+// diagonal class (5..8); S16: S of both classes as 16-bit numbers (axis low),
+// S16g: the g decode scales S / kGScale of both classes, S16g0: that of g_0.
+struct GridCol {
+    float invS_a, G_a, cS_a, S_a;  // 1 / S, kGScale / S, S / 2; S_a
+    float invS_d, G_d, cS_d, pad0;
+    uint32_t S16, S16g, S16g0, pad1;
 };
 
-struct CodecB16 {
+// S_a of column j
+template <class Codec>
+__device__ __forceinline__ float grid_sa(int j) {
+    constexpr uint32_t mask = (1u << (24 - Codec::kScaleBits)) - 1u;
+    const uint32_t u = __float_as_uint(__fmul_rn((float)j + 0.5f, 1.0f / 9.0f));
+    return __uint_as_float((u + mask) & ~mask);
+}
+
+template <class Codec>
+__device__ __forceinline__ GridCol grid_col(int j) {
+    using PT = typename Codec::PT;
+    constexpr float gs = Codec::kGScale;
+    const float Sa = grid_sa<Codec>(j), Sd = 0.25f * Sa, S0 = 4.0f * Sa;
+    const float inv = __frcp_rn(Sa);
+    GridCol g;
+    g.invS_a = inv;
+    g.invS_d = 4.0f * inv;
+    g.G_a = gs * inv;
+    g.G_d = gs * g.invS_d;
+    g.cS_a = 0.5f * Sa;
+    g.cS_d = 0.5f * Sd;
+    g.S_a = Sa;
+    g.pad0 = 0.0f;
+    g.S16 = (uint32_t)bits16(to16<PT>(Sa)) | ((uint32_t)bits16(to16<PT>(Sd)) << 16);
+    g.S16g = (uint32_t)bits16(to16<PT>(Sa / gs)) | ((uint32_t)bits16(to16<PT>(Sd / gs)) << 16);
+    g.S16g0 = (uint32_t)bits16(to16<PT>(S0 / gs));
+    g.pad1 = 0u;
+    return g;
+}
+
+// Rounding of a 16-bit-storage f_0 onto the ledger grid of column j: the
+// multiple of q = 2^-kGridExp ulp(S_5(max(j - 1, 0))) nearest to x (x + 1.5 *
+// 2^23 q - 1.5 * 2^23 q, for |x| < 2^22 q).
+template <class Codec>
+__device__ __forceinline__ float grid_round_f0(float x, int j) {
+    const uint32_t ex = (__float_as_uint(0.25f * grid_sa<Codec>(max(j - 1, 0))) >> 23) & 0xffu;
+    const float m = __uint_as_float(((ex + 24u - Codec::kScaleBits - Codec::kGridExp) << 23) | 0x400000u);
+    return __fadd_rn(__fadd_rn(x, m), -m);
+}
+
+template <class PT_, class PT2_, int kGS, int kE, int kBits>
+struct CodecGrid16 {
     using Real = float;
-    using PT = __nv_bfloat16;
-    using F0T = float2;
-    using PT2 = __nv_bfloat162;
-    static constexpr bool kLedger = true;
+    using PT = PT_;
+    using F0T = float;
+    using PT2 = PT2_;
+    static constexpr bool kLedger = false;
+    static constexpr bool kGrid = true;
     static constexpr bool kStreamStores = true;
-    __device__ static Real dec_f(PT v, Real wr) { return __fmaf_rn(__bfloat162float(v), wr, 0.5f * wr); }
-    __device__ static PT enc_f(Real v, Real, Real inv_wr) { return __float2bfloat16_rn(v * inv_wr - 0.5f); }
-    __device__ static Real dec_g(PT v, Real wr) { return __bfloat162float(v) * wr; }
-    __device__ static PT enc_g(Real v, Real, Real inv_wr) { return __float2bfloat16_rn(v * inv_wr); }
-    __device__ static PT2 enc_pair(Real f, Real g, Real, Real inv_wr) {
-        return __floats2bfloat162_rn(f * inv_wr - 0.5f, g * inv_wr);
+    static constexpr float kGScale = (float)kGS;
+    static constexpr int kGridExp = kE, kScaleBits = kBits;
+    static_assert(kE + kBits <= 16, "ledger sums of at most 24 bits");
+    // x + kMagic - kMagic rounds |x| < 2^(22 - kE) to a multiple of 2^-kE
+    static constexpr float kMagic = 1.5f * (float)(1 << (23 - kE));
+    // D: the diagonal class (directions 5..8), else the axis class (1..4); a
+    // constant wherever it is called (unrolled direction loops)
+    // f_i from its stored value at the column of g
+    __device__ static float dec_f(PT h, const GridCol& g, bool D) {
+        return fma_h(h, (uint16_t)(D ? g.S16 >> 16 : g.S16 & 0xffffu), D ? g.cS_d : g.cS_a);
     }
+    __device__ static float dec_g(PT h, const GridCol& g, bool D) {
+        return fma_h(h, (uint16_t)(D ? g.S16g >> 16 : g.S16g & 0xffffu), 0.0f);
+    }
+    __device__ static float dec_g0(PT h, const GridCol& g) { return fma_h(h, (uint16_t)g.S16g0, 0.0f); }
+    // the stored h of f: f / S - 1/2 on the 2^-kE grid
+    __device__ static float grid_h(float f, const GridCol& g, bool D) {
+        return __fadd_rn(__fmaf_rn(f, D ? g.invS_d : g.invS_a, kMagic - 0.5f), -kMagic);
+    }
+    // f and g of a direction as one stored pair
+    __device__ static PT2 enc_pair(float f, float gv, const GridCol& g, bool D) {
+        PT2 e;
+        e.x = to16<PT>(grid_h(f, g, D));
+        e.y = to16<PT>(gv * (D ? g.G_d : g.G_a));
+        return e;
+    }
+    __device__ static PT enc_f(float f, const GridCol& g, bool D) { return to16<PT>(grid_h(f, g, D)); }
+    __device__ static PT enc_g(float gv, const GridCol& g, bool D) { return to16<PT>(gv * (D ? g.G_d : g.G_a)); }
+    // g_0 (S_0 = 4 S_a)
+    __device__ static PT enc_g0(float gv, const GridCol& g) { return to16<PT>(gv * (0.25f * g.G_a)); }
 };
+// (kGridExp, kScaleBits): measured on the 64 x 128 static drop against the
+// FP64 oracle (2000 steps, phi max / L2): FP16 (12, 4) 3.4e-2 / 7.2e-4,
+// (13, 3) 4.0e-2 / 8.3e-4, (14, 2) 1.7e-2 / 3.5e-4 (the finer grid matters
+// more than alpha near 1); bfloat16 (9, 7) 0.17 / 4.8e-3, (10, 6) 0.10 /
+// 3.3e-3, (11, 5) 0.11 / 2.3e-3, but with (11, 5) the ratio-1000 thread
+// (R0 = 20, k = 0.7) did not pinch off within 30,000 steps and the P2 drop's
+// frequency moved 8.7 % from the FP64 run's, against 2.3 % with (9, 7).
+#ifndef AXILBM_H16_E
+#define AXILBM_H16_E 14
+#define AXILBM_H16_B 2
+#endif
+#ifndef AXILBM_B16_E
+#define AXILBM_B16_E 9
+#define AXILBM_B16_B 7
+#endif
+using CodecH16 = CodecGrid16<__half, __half2, 256, AXILBM_H16_E, AXILBM_H16_B>;
+using CodecB16 = CodecGrid16<__nv_bfloat16, __nv_bfloat162, 1, AXILBM_B16_E, AXILBM_B16_B>;
+
+// phi of a 16-bit node (Eq. 16) from its stored f_0 and h_1..8:
+//   sum f_i / r = (f_0 + S_a (A + B / 4)) / r,  A = 2 + h_1 + .. + h_4,
+//   B = 2 + h_5 + .. + h_8,
+// summed from the stored values with eight mixed-precision adds (no decode);
+// every path that forms phi of a 16-bit node uses this one form, so the phi
+// window is the same whichever tile or launch shape computes a cell.
+template <typename PT>
+__device__ __forceinline__ float phi_grid(float f0, const PT* h, float inv_r, float Sa) {
+    float a = 2.0f, b = 2.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a = add_h(h[i], a);
+#pragma unroll
+    for (int i = 4; i < 8; ++i) b = add_h(h[i], b);
+    return __fmul_rn(__fmaf_rn(Sa, __fmaf_rn(b, 0.25f, a), f0), inv_r);
+}
 
 // f_0 as a value of the arithmetic type.
 __device__ __forceinline__ double f0_value(double v) { return v; }
 __device__ __forceinline__ float f0_value(float2 v) { return v.x + v.y; }
+__device__ __forceinline__ float f0_value(float v) { return v; }
 
 // ---------------------------------------------------------------- storage layout
 // Nodes are stored in groups of 32 consecutive nodes of one row: node L of
@@ -345,14 +457,15 @@ __device__ __forceinline__ int ghost_z(int k, int nz, int zper) {
 }
 
 // phi of a node from its raw stored f_0 (F0T) and f_1..8 (Eq. 16): the
-// plain sum in FP64 and FP32 storage, phi_from_halves in 16-bit storage.
+// plain sum in FP64 and FP32 storage, phi_grid in 16-bit storage (Sa: S_a of
+// the node's column; unused otherwise).
 template <class Codec>
 __device__ __forceinline__ typename Codec::Real phi_of(const typename Codec::F0T& f0raw,
                                                         const typename Codec::PT* fraw,
-                                                        typename Codec::Real inv_r) {
+                                                        typename Codec::Real inv_r, float Sa = 0.0f) {
     using Real = typename Codec::Real;
-    if constexpr (sizeof(typename Codec::PT) == 2) {
-        return phi_from_halves(f0_value(f0raw), fraw, inv_r);
+    if constexpr (Codec::kGrid) {
+        return phi_grid(f0raw, fraw, inv_r, Sa);
     } else {
         Real s = (Real)f0_value(f0raw);
 #pragma unroll
@@ -364,13 +477,14 @@ __device__ __forceinline__ typename Codec::Real phi_of(const typename Codec::F0T
 // phi at an in-domain node from its stored populations (Eq. 16).  FP64 and
 // FP32: each load feeds the running sum (the order phi_of sums in).
 template <class Codec>
-__device__ __forceinline__ typename Codec::Real node_phi(const Node<Codec>& n, typename Codec::Real inv_r) {
+__device__ __forceinline__ typename Codec::Real node_phi(const Node<Codec>& n, typename Codec::Real inv_r,
+                                                          float Sa = 0.0f) {
     using Real = typename Codec::Real;
-    if constexpr (sizeof(typename Codec::PT) == 2) {
+    if constexpr (Codec::kGrid) {
         typename Codec::PT fraw[8];
 #pragma unroll
         for (int i = 1; i < 9; ++i) fraw[i - 1] = n.f(i);
-        return phi_of<Codec>(n.f0(), fraw, inv_r);
+        return phi_grid(n.f0(), fraw, inv_r, Sa);
     } else {
         Real s = (Real)f0_value(n.f0());
 #pragma unroll
@@ -378,12 +492,6 @@ __device__ __forceinline__ typename Codec::Real node_phi(const Node<Codec>& n, t
         return s * inv_r;
     }
 }
-template <class Codec>
-__device__ __forceinline__ typename Codec::Real node_phi(const CaseView<Codec>& V, int loc,
-                                                          typename Codec::Real inv_r) {
-    return node_phi<Codec>(V.in_node(loc), inv_r);
-}
-
 // ---------------------------------------------------------------- arithmetic helpers
 // FP32: the hardware approximate reciprocal, division and square root (a few
 // ulp, far below the FP32 rounding the method accumulates over a run);

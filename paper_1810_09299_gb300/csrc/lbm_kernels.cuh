@@ -16,15 +16,75 @@ constexpr int kTR = 32;  // tile width along r = one warp
 // 3/2 of a wave gives the same time, half a wave or two waves less.
 constexpr int kPrefetchQuarters = 4;
 
-// phi at window position (a, b) of tile t through the ghost rules.
+// Column constants of the 16-bit grid codecs (GridCol) for the window
+// columns b = 0 .. kTR + 3 of a tile (column ghost_r(j0 - 2 + b)), built
+// once per CTA in shared memory as three arrays, so a warp's lookups of
+// consecutive columns are conflict-free 16-byte loads.
+struct GridTab {
+    float4* A;  // invS_a, G_a, cS_a, S_a
+    float4* D;  // invS_d, G_d, cS_d, -
+    uint4* H;   // S16, S16g, S16g0, -
+    __device__ __forceinline__ GridCol col(int b) const {
+        const float4 a = A[b], d = D[b];
+        const uint4 h = H[b];
+        return GridCol{a.x, a.y, a.z, a.w, d.x, d.y, d.z, d.w, h.x, h.y, h.z, h.w};
+    }
+    __device__ __forceinline__ void put(int b, const GridCol& g) const {
+        A[b] = make_float4(g.invS_a, g.G_a, g.cS_a, g.S_a);
+        D[b] = make_float4(g.invS_d, g.G_d, g.cS_d, g.pad0);
+        H[b] = make_uint4(g.S16, g.S16g, g.S16g0, g.pad1);
+    }
+};
+template <class Codec>
+__device__ __forceinline__ void grid_tab_fill(const GridTab& T, int q, int j0, int nr) {
+    if (q < kTR + 4) T.put(q, grid_col<Codec>(ghost_r(j0 - 2 + q, nr)));
+}
+
+// Where node_update takes the column constants of the three columns a node's
+// populations land in (s = 0: the column j - 1, or j on the axis; s = 1: j;
+// s = 2: j + 1, or j at the wall r = nr): none (FP64, FP32), a GridTab, or
+// computed from the column index.
+struct NoCols {
+    __device__ __forceinline__ GridCol get(int) const { return GridCol{}; }
+};
+struct TabCols {
+    GridTab T;
+    int bm, bo, bp;
+    __device__ __forceinline__ GridCol get(int s) const { return T.col(s == 0 ? bm : (s == 1 ? bo : bp)); }
+};
+template <class Codec>
+struct CalcCols {
+    int jm, jo, jp;
+    __device__ __forceinline__ GridCol get(int s) const { return grid_col<Codec>(s == 0 ? jm : (s == 1 ? jo : jp)); }
+};
+
+// phi of node (k, j) at storage index loc, with everything taken from j
+template <class Codec>
+__device__ __forceinline__ typename Codec::Real node_phi_at(const CaseView<Codec>& V, int loc, int j) {
+    using Real = typename Codec::Real;
+    const Real r = (Real)j + (Real)0.5;
+    float Sa = 0.0f;
+    if constexpr (Codec::kGrid) Sa = grid_sa<Codec>(j);
+    return node_phi<Codec>(V.in_node(loc), rcp_(r), Sa);
+}
+
+// phi at window position (a, b) of tile t through the ghost rules; T: the
+// tile's GridTab when there is one (16-bit storage), else P and c of the
+// column are computed.
 template <class Codec>
 __device__ __forceinline__ typename Codec::Real window_phi(const CaseDev& C, const CaseView<Codec>& V,
-                                                            const TileDev& t, int a, int b) {
+                                                            const TileDev& t, int a, int b,
+                                                            const GridTab* T = nullptr) {
     using Real = typename Codec::Real;
     const int k = ghost_z(t.k0 - 2 + a, C.nz, C.zper);
     const int j = ghost_r(t.j0 - 2 + b, C.nr);
-    const Real r = (Real)j + (Real)0.5;
-    return node_phi<Codec>(V, k * C.pitch + j, rcp_(r));
+    if constexpr (Codec::kGrid) {
+        if (T != nullptr) {
+            const Real r = (Real)j + (Real)0.5;
+            return node_phi<Codec>(V.in_node(k * C.pitch + j), rcp_(r), T->A[b].w);
+        }
+    }
+    return node_phi_at<Codec>(V, k * C.pitch + j, j);
 }
 
 // The ring of a tile's phi window: the two rows above and below the tile and
@@ -61,9 +121,14 @@ __device__ __forceinline__ void ring_cell(int q, int& a, int& b) {
 #ifndef AXILBM_GENERAL_CTAS
 #define AXILBM_GENERAL_CTAS 4
 #endif
+#ifndef AXILBM_STEP16_CTAS
+#define AXILBM_STEP16_CTAS 5
+#endif
 template <class Codec, int BZ, int RM>
 constexpr int step_min_blocks() {
-    constexpr int bz8 = (RM == kRatesPaperRaw && sizeof(typename Codec::PT) == 2) ? 4 : 5;
+    constexpr int bz8 = (RM == kRatesPaperRaw && sizeof(typename Codec::PT) == 2)
+                            ? 4
+                            : (sizeof(typename Codec::PT) == 2 ? AXILBM_STEP16_CTAS : 5);
     return sizeof(typename Codec::Real) == 8 ? 1
            : RM != kRatesGeneral ? (BZ >= 16 ? 2 : (BZ >= 8 ? bz8 : 8))
                 : (BZ >= 16 ? 1 : (BZ >= 8 ? AXILBM_GENERAL_CTAS : 2 * AXILBM_GENERAL_CTAS));
@@ -81,6 +146,31 @@ __device__ __forceinline__ typename Codec::Real store_pair(typename Codec::PT2* 
     if constexpr (Codec::kStreamStores) __stcs(dst, e);
     else *dst = e;
     return Codec::dec_f(e.x, wr);
+}
+// The same for the 16-bit grid codecs, with the destination column's constants.
+template <class Codec>
+__device__ __forceinline__ float store_pair_grid(typename Codec::PT2* dst, const GridCol& g, bool D, float fpi,
+                                                 float gpi) {
+    const typename Codec::PT2 e = Codec::enc_pair(fpi, gpi, g, D);
+    if constexpr (Codec::kStreamStores) __stcs(dst, e);
+    else *dst = e;
+    return Codec::dec_f(e.x, g, D);
+}
+
+// Direction I's store of the branch-free push in either storage form: the
+// radii rdst / rinv (s = cr_of(I) + 1) or the column constants cols.get(s).
+template <class Codec, int I, class Cols>
+__device__ __forceinline__ typename Codec::Real store_dir(typename Codec::PT2* dst, const Cols& cols,
+                                                          const typename Codec::Real* rdst,
+                                                          const typename Codec::Real* rinv, typename Codec::Real f,
+                                                          typename Codec::Real g) {
+    using Real = typename Codec::Real;
+    if constexpr (Codec::kGrid) {
+        return store_pair_grid<Codec>(dst, cols.get(cr_of(I) + 1), I > 4, f, g);
+    } else {
+        return store_pair<Codec>(dst, (Real)w_of(I) * rdst[cr_of(I) + 1], (Real)(1.0 / w_of(I)) * rinv[cr_of(I) + 1],
+                                 f, g);
+    }
 }
 
 // Byte offset of direction d's pair slot inside a node group's block.
@@ -107,12 +197,13 @@ __device__ __forceinline__ int push_offset(bool axis, bool wall, int rowp, int r
 }
 
 // What the collisions take from a node's own populations: the moments M f and
-// M g, g_0, and the mass ledger's incoming total.  The ledger is two
-// double-float lanes (f_0 with f_1..4, and f_5..8) advanced together, exact.
-// Decoded populations die here, which keeps the register pressure of the
-// collisions down (measured: no spills at 64 registers, 22 fewer
-// instructions per node in 16-bit storage).  fdec: f_0..8 already decoded by
-// the caller (it summed them for phi), else decoded here.
+// M g, g_0, and the FP32 mass ledger's incoming total.  The FP32 ledger is two
+// double-float lanes (f_0 with f_1..4, and f_5..8) advanced together, exact;
+// in 16-bit storage M f's first moment is the ledger's incoming total itself
+// (exact sums on the grid).  Decoded populations die here, which keeps the
+// register pressure of the collisions down.  fdec: f_0..8 already decoded by
+// the caller (it summed them for phi), else decoded here.  go: the node's own
+// column constants (16-bit storage).
 template <typename Real>
 struct PreCollision {
     Real mf[9], mg[9];
@@ -122,21 +213,29 @@ struct PreCollision {
 template <class Codec>
 __device__ __forceinline__ void node_pre(const typename Codec::F0T& f0raw, const typename Codec::PT* fraw,
                                          const typename Codec::PT* graw, typename Codec::Real r,
-                                         PreCollision<typename Codec::Real>& P,
-                                         const typename Codec::Real* fdec = nullptr) {
+                                         PreCollision<typename Codec::Real>& P, const typename Codec::Real* fdec,
+                                         const GridCol& go) {
     using Real = typename Codec::Real;
-    Real f[9];
+    Real f[9], g[9];
     if (fdec != nullptr) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = fdec[i];
     } else {
         f[0] = (Real)f0_value(f0raw);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) f[i] = Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
+        for (int i = 1; i < 9; ++i) {
+            if constexpr (Codec::kGrid) f[i] = Codec::dec_f(fraw[i - 1], go, i > 4);
+            else f[i] = Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
+        }
     }
-    Real g[9];
+    if constexpr (Codec::kGrid) {
+        g[0] = Codec::dec_g0(graw[0], go);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = Codec::dec_g(graw[i], (Real)w_of(i) * r);
+        for (int i = 1; i < 9; ++i) g[i] = Codec::dec_g(graw[i], go, i > 4);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = Codec::dec_g(graw[i], (Real)w_of(i) * r);
+    }
     moments_fg(f, g, P.mf, P.mg);
     P.g0 = g[0];
     P.ledger = FF2{};
@@ -151,19 +250,20 @@ __device__ __forceinline__ void node_pre(const typename Codec::F0T& f0raw, const
 // macroscopic recovery, both collisions, and the push with the boundary rules.
 // invr: when not null, 1 / r of window column b - 1, b, b + 1 at invr[b - 1 ..
 // b + 1] (the same quotients the node would compute itself).  fdec: see
-// node_pre.
-template <class Codec, int RM, int LD>
+// node_pre.  cols: the column constants of the 16-bit grid codecs (NoCols
+// otherwise).
+template <class Codec, int RM, int LD, class Cols>
 __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Codec>& V, const typename Codec::Real* sphi,
                                             int a, int b, int k, int j, int loc,
                                             const typename Codec::F0T& f0raw, const typename Codec::PT* fraw,
                                             const typename Codec::PT* graw, typename Codec::Real chz_prev,
                                             typename Codec::Real chr_prev, typename Codec::Real p_prev,
-                                            const typename Codec::Real* invr = nullptr,
-                                            const typename Codec::Real* fdec = nullptr) {
+                                            const typename Codec::Real* invr, const typename Codec::Real* fdec,
+                                            const Cols& cols) {
     using Real = typename Codec::Real;
     const Real r = (Real)j + (Real)0.5;
     PreCollision<Real> pre;
-    node_pre<Codec>(f0raw, fraw, graw, r, pre, fdec);
+    node_pre<Codec>(f0raw, fraw, graw, r, pre, fdec, cols.get(1));
     const Real* mf = pre.mf;
     Macro<Real> m;
     node_macros<Real, LD, RM, sizeof(typename Codec::PT) == 2>(C, sphi, a, b, j, pre.mg, pre.g0, p_prev, m,
@@ -180,11 +280,11 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     Real fp[9], gp[9];
     inverse_moments_fg(mpf, mpg, fp, gp);
     // 5. streaming (Eq. 20).  Rows j-1, j, j+1 are the only destinations, so
-    //    three radii serve every normalisation.  On the axis every link with
-    //    c_r < 0 ends in the node's own row (mirror) or at the node itself
-    //    (bounce-back), and on the wall r = nr every link with c_r > 0 returns
-    //    to the node, so there the row's own radius takes the place of the
-    //    missing neighbour row.
+    //    three radii (three columns' constants in 16-bit storage) serve every
+    //    normalisation.  On the axis every link with c_r < 0 ends in the
+    //    node's own row (mirror) or at the node itself (bounce-back), and on
+    //    the wall r = nr every link with c_r > 0 returns to the node, so there
+    //    the row's own radius takes the place of the missing neighbour row.
     const bool axis = (j == 0), wall = (j + 1 == C.nr), zlo = (k == 0), zhi = (k + 1 == C.nz);
     const Real rinv[3] = {axis ? m.inv_r : (invr ? invr[b - 1] : rcp_(r - (Real)1)), m.inv_r,
                           wall ? m.inv_r : (invr ? invr[b + 1] : rcp_(r + (Real)1))};
@@ -196,6 +296,9 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     const int row = (C.pitch >> 5) * kB;         // one z row of blocks
     const int step_r = lane == 31 ? kB - 31 * kPS : kPS;
     const int step_l = lane == 0 ? -(kB - 31 * kPS) : -kPS;
+    // 16-bit grid codecs: the ledger is M f's first moment minus the stored
+    // outgoing f_1..8 (exact), summed by direction pairs (i, i + 4)
+    float2 out_acc;
     if ((zlo || zhi) && !C.zper) {
         // A z-wall row (the whole warp: a warp is one row of a tile): every
         // link by the rules of destination().
@@ -204,10 +307,14 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     {                                                                                                  \
         const Dest d = destination<I>(k, j, C.nr, C.nz, C.zper);                                       \
         const int s = d.j - j + 1;                                                                     \
-        const Real rd = s == 0 ? rdst[0] : (s == 1 ? rdst[1] : rdst[2]);                               \
-        const Real ri = s == 0 ? rinv[0] : (s == 1 ? rinv[1] : rinv[2]);                               \
-        fs[I] = store_pair<Codec>(&V.out_pt(d.k * C.pitch + d.j).pair(d.dir), (Real)w_of(I) * rd,      \
-                                  (Real)(1.0 / w_of(I)) * ri, fp[I], gp[I]);                           \
+        PT2* const dst = &V.out_pt(d.k * C.pitch + d.j).pair(d.dir);                                   \
+        if constexpr (Codec::kGrid) {                                                                  \
+            fs[I] = store_pair_grid<Codec>(dst, cols.get(s), (I) > 4, fp[I], gp[I]);                    \
+        } else {                                                                                       \
+            const Real rd = s == 0 ? rdst[0] : (s == 1 ? rdst[1] : rdst[2]);                           \
+            const Real ri = s == 0 ? rinv[0] : (s == 1 ? rinv[1] : rinv[2]);                           \
+            fs[I] = store_pair<Codec>(dst, (Real)w_of(I) * rd, (Real)(1.0 / w_of(I)) * ri, fp[I], gp[I]); \
+        }                                                                                              \
     }
         AXILBM_PUSH(1)
         AXILBM_PUSH(2)
@@ -218,9 +325,11 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
         AXILBM_PUSH(7)
         AXILBM_PUSH(8)
 #undef AXILBM_PUSH
-        if constexpr (Codec::kLedger) {
 #pragma unroll
-            for (int i = 1; i < 5; ++i) ff2_sub(ledger, make_float2((float)fs[i], (float)fs[i + 4]));
+        for (int i = 1; i < 5; ++i) {
+            if constexpr (Codec::kLedger) ff2_sub(ledger, make_float2((float)fs[i], (float)fs[i + 4]));
+            if constexpr (Codec::kGrid)
+                out_acc = i == 1 ? make_float2(fs[i], fs[i + 4]) : p_add(out_acc, make_float2(fs[i], fs[i + 4]));
         }
     } else {
         // Every other node, branch-free: the axis and wall lanes differ from
@@ -229,14 +338,13 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
         // pair of directions (i, i + 4) as soon as both are stored.
         const int rowp = zhi ? -(C.nz - 1) * row : row;
         const int rowm = zlo ? (C.nz - 1) * row : -row;
-#define AXILBM_STORE(I)                                                                                      \
-    store_pair<Codec>(                                                                                       \
-        reinterpret_cast<PT2*>(q0 + push_offset<Codec, I>(axis, wall, rowp, rowm, step_r, step_l)),          \
-        (Real)w_of(I) * rdst[cr_of(I) + 1], (Real)(1.0 / w_of(I)) * rinv[cr_of(I) + 1], fp[I], gp[I])
-#define AXILBM_STORE_TWO(I)                                                                  \
-    {                                                                                        \
-        const Real fa = AXILBM_STORE(I), fb = AXILBM_STORE(I + 4);                           \
-        if constexpr (Codec::kLedger) ff2_sub(ledger, make_float2((float)fa, (float)fb));    \
+#define AXILBM_DST(I) reinterpret_cast<PT2*>(q0 + push_offset<Codec, I>(axis, wall, rowp, rowm, step_r, step_l))
+#define AXILBM_STORE(I) store_dir<Codec, I>(AXILBM_DST(I), cols, rdst, rinv, fp[I], gp[I])
+#define AXILBM_STORE_TWO(I)                                                                              \
+    {                                                                                                    \
+        const Real fa = AXILBM_STORE(I), fb = AXILBM_STORE(I + 4);                                       \
+        if constexpr (Codec::kLedger) ff2_sub(ledger, make_float2((float)fa, (float)fb));                \
+        if constexpr (Codec::kGrid) out_acc = (I) == 1 ? make_float2(fa, fb) : p_add(out_acc, make_float2(fa, fb)); \
     }
         AXILBM_STORE_TWO(1)
         AXILBM_STORE_TWO(2)
@@ -244,16 +352,21 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
         AXILBM_STORE_TWO(4)
 #undef AXILBM_STORE_TWO
 #undef AXILBM_STORE
+#undef AXILBM_DST
     }
     // the rest direction: g_0 stays at the node
     {
-        const typename Codec::PT e0 = Codec::enc_g(gp[0], (Real)w_of(0) * r, (Real)(1.0 / w_of(0)) * m.inv_r);
+        typename Codec::PT e0;
+        if constexpr (Codec::kGrid) e0 = Codec::enc_g0(gp[0], cols.get(1));
+        else e0 = Codec::enc_g(gp[0], (Real)w_of(0) * r, (Real)(1.0 / w_of(0)) * m.inv_r);
         if constexpr (Codec::kStreamStores) __stcs(&own.g(0), e0);
         else own.g(0) = e0;
     }
     // f_0: the collision's value (FP64), or the mass ledger: incoming total
     // minus the outgoing f_1..8 as they will be read back
-    if constexpr (Codec::kLedger) {
+    if constexpr (Codec::kGrid) {
+        own.f0() = __fsub_rn(mf[0], __fadd_rn(out_acc.x, out_acc.y));
+    } else if constexpr (Codec::kLedger) {
         const FF l = ff2_merge(ledger);
         own.f0() = make_float2(l.hi, l.lo);
     } else {
@@ -287,25 +400,30 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     // FP64 pipe); the same correctly rounded quotients the nodes would form
     constexpr bool kInvrTable = sizeof(Real) == 8;
     __shared__ Real s_invr[kInvrTable ? LD : 1];
+    // 16-bit storage: the column constants of the window's columns
+    constexpr bool kG = Codec::kGrid;
+    __shared__ float4 sgA[kG ? LD : 1], sgD[kG ? LD : 1];
+    __shared__ uint4 sgH[kG ? LD : 1];
+    const GridTab T{sgA, sgD, sgH};
     const TileDev t = tiles[blockIdx.x];
+    const int q = threadIdx.y * kTR + threadIdx.x;
     if constexpr (kInvrTable) {
-        const int q = threadIdx.y * kTR + threadIdx.x;
         if (q < LD) s_invr[q] = (Real)1 / ((Real)(t.j0 - 2 + q) + (Real)0.5);
+    }
+    if constexpr (kG) {
+        if (q < LD) grid_tab_fill<Codec>(T, q, t.j0, cases[t.c].nr);
     }
     // L2 prefetch of the blocks of the tile one resident wave ahead (a CTA
     // that will start about when this one ends): one tensor prefetch, issued
     // by one thread; the tensor maps are absent when they could not be made
-    if (maps != nullptr && threadIdx.x == 0 && threadIdx.y == 0 && (int)blockIdx.x + ahead < ntiles) {
+    if (maps != nullptr && q == 0 && (int)blockIdx.x + ahead < ntiles) {
         const TileDev tp = tiles[blockIdx.x + ahead];
         const CUtensorMap* M = maps + ((size_t)tp.c * 2 + map_set) * kMapsPerCase + 2 + parity;
         tensormap_acquire(M);
         tma_prefetch_4d(M, 0, 0, tp.j0 >> 5, tp.k0);
     }
-    {
-        const int q = threadIdx.y * kTR + threadIdx.x;
-        if (q < (int)(sizeof(CaseDev) / 4))
-            reinterpret_cast<int32_t*>(&sC)[q] = reinterpret_cast<const int32_t*>(cases + t.c)[q];
-    }
+    if (q < (int)(sizeof(CaseDev) / 4))
+        reinterpret_cast<int32_t*>(&sC)[q] = reinterpret_cast<const int32_t*>(cases + t.c)[q];
     __syncthreads();
     const CaseDev& C = sC;
     const CaseView<Codec> V = case_view<Codec>(S, C);
@@ -334,38 +452,51 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     }
     // 2. the ring of the phi window (two rows above and below, two columns
     //    left and right of the tile)
-    for (int q = threadIdx.y * kTR + threadIdx.x; q < NRING; q += kTR * BZ) {
+    for (int qq = q; qq < NRING; qq += kTR * BZ) {
         int a, b;
-        ring_cell<TZ>(q, a, b);
-        sphi[a * LD + b] = window_phi<Codec>(C, V, t, a, b);
+        ring_cell<TZ>(qq, a, b);
+        sphi[a * LD + b] = window_phi<Codec>(C, V, t, a, b, kG ? &T : nullptr);
     }
     // 3. the node's own phi (Eq. 16); window cells outside the domain take the ghost rule
     const Real r = (Real)j + (Real)0.5;
+    const int bo = threadIdx.x + 2;
     Real f[9];
     // 16-bit storage: the decoded f live on across the barrier (measured
     // -1.5 % against decoding them again; +0.6 % in FP32, where decoding is
     // free)
     constexpr bool kKeepF = sizeof(PT) == 2;
     if (inside) {
-        f[0] = (Real)f0_value(f0raw);
-        Real sum = f[0];
+        const Real inv_r = kInvrTable ? s_invr[bo] : rcp_(r);
+        if constexpr (kG) {
+            const GridCol g = T.col(bo);
+            f[0] = f0raw;
 #pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            f[i] = Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
-            sum += f[i];
+            for (int i = 1; i < 9; ++i) f[i] = Codec::dec_f(fraw[i - 1], g, i > 4);
+            sphi[(threadIdx.y + 2) * LD + bo] = phi_of<Codec>(f0raw, fraw, inv_r, g.S_a);
+        } else {
+            f[0] = (Real)f0_value(f0raw);
+            Real sum = f[0];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                f[i] = Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
+                sum += f[i];
+            }
+            sphi[(threadIdx.y + 2) * LD + bo] = sum * inv_r;
         }
-        const Real inv_r = kInvrTable ? s_invr[threadIdx.x + 2] : rcp_(r);
-        // 16-bit storage: phi in the one form of phi_of (sum unused)
-        sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] =
-            kKeepF ? phi_of<Codec>(f0raw, fraw, inv_r) : sum * inv_r;
     } else {
-        sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = window_phi<Codec>(C, V, t, threadIdx.y + 2, threadIdx.x + 2);
+        sphi[(threadIdx.y + 2) * LD + bo] = window_phi<Codec>(C, V, t, threadIdx.y + 2, bo, kG ? &T : nullptr);
     }
     __syncthreads();
     if (!inside) return;
 
-    node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw, graw, chz_prev,
-                               chr_prev, p_prev, kInvrTable ? s_invr : nullptr, kKeepF ? f : nullptr);
+    if constexpr (kG) {
+        const TabCols cols{T, j == 0 ? bo : bo - 1, bo, j + 1 == C.nr ? bo : bo + 1};
+        node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2, bo, k, j, loc, f0raw, fraw, graw, chz_prev,
+                                   chr_prev, p_prev, nullptr, f, cols);
+    } else {
+        node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2, bo, k, j, loc, f0raw, fraw, graw, chz_prev,
+                                   chr_prev, p_prev, kInvrTable ? s_invr : nullptr, kKeepF ? f : nullptr, NoCols{});
+    }
 }
 
 // The step with two nodes per thread, one after the other: thread (x, y) of
@@ -397,7 +528,15 @@ step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
     __shared__ Real sphi[(TZ + 4) * LD];
     __shared__ __align__(16) CaseDev sC;
     static_assert(sizeof(CaseDev) % 4 == 0 && sizeof(CaseDev) / 4 <= kTR * BZ, "one word per thread");
+    constexpr bool kG = Codec::kGrid;
+    __shared__ float4 sgA[kG ? LD : 1], sgD[kG ? LD : 1];
+    __shared__ uint4 sgH[kG ? LD : 1];
+    const GridTab T{sgA, sgD, sgH};
     const TileDev t = tiles[blockIdx.x];
+    if constexpr (kG) {
+        const int q = threadIdx.y * kTR + threadIdx.x;
+        if (q < LD) grid_tab_fill<Codec>(T, q, t.j0, cases[t.c].nr);
+    }
     if (maps != nullptr && threadIdx.x == 0 && threadIdx.y == 0 && (int)blockIdx.x + ahead < ntiles) {
         const TileDev tp = tiles[blockIdx.x + ahead];
         const CUtensorMap* M = maps + ((size_t)tp.c * 2 + map_set) * kMapsPerCase + 2 + parity;
@@ -441,21 +580,25 @@ step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
     for (int q = threadIdx.y * kTR + threadIdx.x; q < NRING; q += kTR * BZ) {
         int a, b;
         ring_cell<TZ>(q, a, b);
-        sphi[a * LD + b] = window_phi<Codec>(C, V, t, a, b);
+        sphi[a * LD + b] = window_phi<Codec>(C, V, t, a, b, kG ? &T : nullptr);
     }
     // 3. both nodes' own phi (Eq. 16), in the form of the one-node kernel
     const Real r = (Real)j + (Real)0.5;
+    const int bo = threadIdx.x + 2;
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int a = threadIdx.y + 2 + p * BZ;
         if (in[p]) {
-            Real sum = (Real)f0_value(f0raw[p]);
+            if constexpr (kG) {
+                sphi[a * LD + bo] = phi_of<Codec>(f0raw[p], fraw[p], rcp_(r), T.A[bo].w);
+            } else {
+                Real sum = (Real)f0_value(f0raw[p]);
 #pragma unroll
-            for (int i = 1; i < 9; ++i) sum += Codec::dec_f(fraw[p][i - 1], (Real)w_of(i) * r);
-            sphi[a * LD + threadIdx.x + 2] =
-                sizeof(PT) == 2 ? phi_of<Codec>(f0raw[p], fraw[p], rcp_(r)) : sum * rcp_(r);
+                for (int i = 1; i < 9; ++i) sum += Codec::dec_f(fraw[p][i - 1], (Real)w_of(i) * r);
+                sphi[a * LD + bo] = sum * rcp_(r);
+            }
         } else {
-            sphi[a * LD + threadIdx.x + 2] = window_phi<Codec>(C, V, t, a, threadIdx.x + 2);
+            sphi[a * LD + bo] = window_phi<Codec>(C, V, t, a, bo, kG ? &T : nullptr);
         }
     }
     __syncthreads();
@@ -463,8 +606,15 @@ step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
     for (int p = 0; p < 2; ++p) {
         if (!in[p]) continue;
         const int k = t.k0 + threadIdx.y + p * BZ;
-        node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2 + p * BZ, threadIdx.x + 2, k, j, k * C.pitch + j,
-                                   f0raw[p], fraw[p], graw[p], chz_prev[p], chr_prev[p], p_prev[p]);
+        if constexpr (kG) {
+            const TabCols cols{T, j == 0 ? bo : bo - 1, bo, j + 1 == C.nr ? bo : bo + 1};
+            node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2 + p * BZ, bo, k, j, k * C.pitch + j, f0raw[p],
+                                       fraw[p], graw[p], chz_prev[p], chr_prev[p], p_prev[p], nullptr, nullptr, cols);
+        } else {
+            node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2 + p * BZ, bo, k, j, k * C.pitch + j, f0raw[p],
+                                       fraw[p], graw[p], chz_prev[p], chr_prev[p], p_prev[p], nullptr, nullptr,
+                                       NoCols{});
+        }
     }
 }
 
@@ -526,11 +676,13 @@ __device__ __forceinline__ typename Codec::Real staged_phi(const unsigned char* 
     const int jm = ghost_r(tt.j0 - 2 + b, C.nr);
     const int sa = km - (tt.k0 - 2);
     const Real r = (Real)jm + (Real)0.5;
+    float Sa = 0.0f;
+    if constexpr (Codec::kGrid) Sa = grid_sa<Codec>(jm);
     if (sa >= 0 && sa < L::HR && (jm >> 5) == (tt.j0 >> 5)) {
         const Node<Codec> n{const_cast<unsigned char*>(st + L::off_box) + (size_t)sa * Block<Codec>::bytes, jm & 31};
-        return node_phi<Codec>(n, rcp_(r));
+        return node_phi<Codec>(n, rcp_(r), Sa);
     }
-    return node_phi<Codec>(V, km * C.pitch + jm, rcp_(r));
+    return node_phi<Codec>(V.in_node(km * C.pitch + jm), rcp_(r), Sa);
 }
 
 // Resident CTAs per SM: as many as the stages' shared memory allows (up to
@@ -634,15 +786,22 @@ step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
         const Real r = (Real)j + (Real)0.5;
         Real f[9];
         if (inside) {
-            f[0] = (Real)f0_value(f0raw);
-            Real sum = f[0];
+            if constexpr (Codec::kGrid) {
+                const GridCol g = grid_col<Codec>(j);
+                f[0] = f0raw;
 #pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                f[i] = Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
-                sum += f[i];
+                for (int i = 1; i < 9; ++i) f[i] = Codec::dec_f(fraw[i - 1], g, i > 4);
+                sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = phi_of<Codec>(f0raw, fraw, rcp_(r), g.S_a);
+            } else {
+                f[0] = (Real)f0_value(f0raw);
+                Real sum = f[0];
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    f[i] = Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
+                    sum += f[i];
+                }
+                sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = sum * rcp_(r);
             }
-            sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] =
-                sizeof(PT) == 2 ? phi_of<Codec>(f0raw, fraw, rcp_(r)) : sum * rcp_(r);
         } else {
             sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] =
                 staged_phi<Codec, TZ>(st, C, V, tt, threadIdx.y + 2, threadIdx.x + 2);
@@ -650,8 +809,14 @@ step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
         __syncthreads();
         if (inside) {
             const int loc = k * C.pitch + j;
-            node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw, graw,
-                                       chz_prev, chr_prev, p_prev, nullptr, sizeof(PT) == 2 ? f : nullptr);
+            if constexpr (Codec::kGrid) {
+                const CalcCols<Codec> cols{j == 0 ? j : j - 1, j, j + 1 == C.nr ? j : j + 1};
+                node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw,
+                                           graw, chz_prev, chr_prev, p_prev, nullptr, f, cols);
+            } else {
+                node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw,
+                                           graw, chz_prev, chr_prev, p_prev, nullptr, nullptr, NoCols{});
+            }
         }
         if (NS == 1) {
             // every read of the single stage is done before it is refilled
@@ -686,8 +851,15 @@ fields_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ til
     const Real r = (Real)j + (Real)0.5;
     const Node<Codec> nd = V.in_node(loc);
     Real g[9];
+    if constexpr (Codec::kGrid) {
+        const GridCol gc = grid_col<Codec>(j);
+        g[0] = Codec::dec_g0(nd.g(0), gc);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = Codec::dec_g(nd.g(i), (Real)w_of(i) * r);
+        for (int i = 1; i < 9; ++i) g[i] = Codec::dec_g(nd.g(i), gc, i > 4);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = Codec::dec_g(nd.g(i), (Real)w_of(i) * r);
+    }
     Macro<Real> m;
     Real mg[9];
     moments<Real>(g, mg);
@@ -720,21 +892,39 @@ __device__ __forceinline__ void init_node(const CaseDev& C, const StateDev<Codec
         fe[i] = (Real)w_of(i) * (r * phi + (Real)cr_of(i) * P.mob * phi * (Real)3);
         if constexpr (Codec::kLedger) ff_add(ledger, (float)fe[i]);
     }
+    if constexpr (Codec::kGrid) {
+        // f_0 takes the rest of the node's total, rounded onto its ledger grid
+        const GridCol g = grid_col<Codec>(j);
+        float rest = 0.0f;
 #pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        const Real wr = (Real)w_of(i) * r;
-        const auto e = Codec::enc_f(fe[i], wr, (Real)1 / wr);
-        n.f(i) = e;
-        if constexpr (Codec::kLedger) ff_add(ledger, -(float)Codec::dec_f(e, wr));
-    }
-    if constexpr (Codec::kLedger) {
-        const FF l = ff_norm(ledger);
-        n.f0() = make_float2(l.hi, l.lo);
+        for (int i = 0; i < 9; ++i) rest += fe[i];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const auto e = Codec::enc_f(fe[i], g, i > 4);
+            n.f(i) = e;
+            rest -= Codec::dec_f(e, g, i > 4);
+        }
+        n.f0() = grid_round_f0<Codec>(rest, j);
+        n.g(0) = Codec::enc_g0((Real)0, g);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) n.g(i) = Codec::enc_g((Real)0, g, i > 4);
     } else {
-        n.f0() = fe[0];
-    }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) n.g(i) = Codec::enc_g((Real)0, (Real)w_of(i) * r, (Real)1);
+        for (int i = 1; i < 9; ++i) {
+            const Real wr = (Real)w_of(i) * r;
+            const auto e = Codec::enc_f(fe[i], wr, (Real)1 / wr);
+            n.f(i) = e;
+            if constexpr (Codec::kLedger) ff_add(ledger, -(float)Codec::dec_f(e, wr));
+        }
+        if constexpr (Codec::kLedger) {
+            const FF l = ff_norm(ledger);
+            n.f0() = make_float2(l.hi, l.lo);
+        } else {
+            n.f0() = fe[0];
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) n.g(i) = Codec::enc_g((Real)0, (Real)w_of(i) * r, (Real)1);
+    }
     n.chz() = (Real)0;
     n.chr() = P.mob * phi;
     n.p() = (Real)0;
@@ -767,17 +957,29 @@ __global__ void get_state_kernel(CaseDev C, StateDev<Codec> S, double* f, double
     const Node<Codec> nd = V.in_node(k * C.pitch + j);
     const int64_t n = (int64_t)C.nz * C.nr, o = (int64_t)k * C.nr + j;
     const Real r = (Real)j + (Real)0.5;
-    if (f) {
-        if constexpr (Codec::kLedger) {
-            const float2 v = nd.f0();
-            f[o] = (double)v.x + (double)v.y;
-        } else {
-            f[o] = (double)f0_value(nd.f0());
+    if constexpr (Codec::kGrid) {
+        const GridCol gc = grid_col<Codec>(j);
+        if (f) {
+            f[o] = (double)nd.f0();
+            for (int i = 1; i < 9; ++i) f[i * n + o] = (double)Codec::dec_f(nd.f(i), gc, i > 4);
         }
-        for (int i = 1; i < 9; ++i) f[i * n + o] = (double)Codec::dec_f(nd.f(i), (Real)w_of(i) * r);
-    }
-    if (g) {
-        for (int i = 0; i < 9; ++i) g[i * n + o] = (double)Codec::dec_g(nd.g(i), (Real)w_of(i) * r);
+        if (g) {
+            g[o] = (double)Codec::dec_g0(nd.g(0), gc);
+            for (int i = 1; i < 9; ++i) g[i * n + o] = (double)Codec::dec_g(nd.g(i), gc, i > 4);
+        }
+    } else {
+        if (f) {
+            if constexpr (Codec::kLedger) {
+                const float2 v = nd.f0();
+                f[o] = (double)v.x + (double)v.y;
+            } else {
+                f[o] = (double)f0_value(nd.f0());
+            }
+            for (int i = 1; i < 9; ++i) f[i * n + o] = (double)Codec::dec_f(nd.f(i), (Real)w_of(i) * r);
+        }
+        if (g) {
+            for (int i = 0; i < 9; ++i) g[i * n + o] = (double)Codec::dec_g(nd.g(i), (Real)w_of(i) * r);
+        }
     }
     if (aux) {
         aux[o] = (double)nd.chz();
@@ -797,34 +999,58 @@ __global__ void set_state_kernel(CaseDev C, StateDev<Codec> S, const double* f, 
     const Node<Codec> nd = V.in_node(k * C.pitch + j);
     const int64_t n = (int64_t)C.nz * C.nr, o = (int64_t)k * C.nr + j;
     const Real r = (Real)j + (Real)0.5;
-    if (f) {
-        if constexpr (Codec::kLedger) {
-            // ledger = f_0 exactly as given (split into a float pair) plus the
-            // rounding of f_1..8, so the stored populations sum to the input sum
-            const double v0 = f[o];
-            FF ledger{(float)v0, (float)(v0 - (double)(float)v0)};
+    if constexpr (Codec::kGrid) {
+        const GridCol gc = grid_col<Codec>(j);
+        if (f) {
+            // f_0 = the given f_0 plus the rounding of f_1..8 (in FP64), on the
+            // node's ledger grid: the stored populations sum to the input sum
+            // up to that last rounding
+            double v = f[o];
             for (int i = 1; i < 9; ++i) {
-                const Real wr = (Real)w_of(i) * r;
-                const auto e = Codec::enc_f((Real)f[i * n + o], wr, (Real)1 / wr);
+                const auto e = Codec::enc_f((float)f[i * n + o], gc, i > 4);
                 nd.f(i) = e;
-                ff_add(ledger, (float)f[i * n + o]);
-                ff_add(ledger, (float)(f[i * n + o] - (double)(float)f[i * n + o]));
-                ff_add(ledger, -(float)Codec::dec_f(e, wr));
+                v += f[i * n + o] - (double)Codec::dec_f(e, gc, i > 4);
             }
-            const FF l = ff_norm(ledger);
-            *reinterpret_cast<float2*>(&nd.f0()) = make_float2(l.hi, l.lo);
-        } else {
-            for (int i = 1; i < 9; ++i) {
-                const Real wr = (Real)w_of(i) * r;
-                nd.f(i) = Codec::enc_f((Real)f[i * n + o], wr, (Real)1 / wr);
-            }
-            *reinterpret_cast<double*>(&nd.f0()) = f[o];
+            // the ledger grid q = 2^-kGridExp ulp(S_5(max(j - 1, 0))) at kScaleBits bits
+            int ex = 0;
+            frexp((double)(0.25f * grid_sa<Codec>(max(j - 1, 0))), &ex);
+            const double q = ldexp(1.0, ex - Codec::kScaleBits - Codec::kGridExp);
+            nd.f0() = (float)(rint(v / q) * q);
         }
-    }
-    if (g) {
-        for (int i = 0; i < 9; ++i) {
-            const Real wr = (Real)w_of(i) * r;
-            nd.g(i) = Codec::enc_g((Real)g[i * n + o], wr, (Real)1 / wr);
+        if (g) {
+            nd.g(0) = Codec::enc_g0((float)g[o], gc);
+            for (int i = 1; i < 9; ++i) nd.g(i) = Codec::enc_g((float)g[i * n + o], gc, i > 4);
+        }
+    } else {
+        if (f) {
+            if constexpr (Codec::kLedger) {
+                // ledger = f_0 exactly as given (split into a float pair) plus the
+                // rounding of f_1..8, so the stored populations sum to the input sum
+                const double v0 = f[o];
+                FF ledger{(float)v0, (float)(v0 - (double)(float)v0)};
+                for (int i = 1; i < 9; ++i) {
+                    const Real wr = (Real)w_of(i) * r;
+                    const auto e = Codec::enc_f((Real)f[i * n + o], wr, (Real)1 / wr);
+                    nd.f(i) = e;
+                    ff_add(ledger, (float)f[i * n + o]);
+                    ff_add(ledger, (float)(f[i * n + o] - (double)(float)f[i * n + o]));
+                    ff_add(ledger, -(float)Codec::dec_f(e, wr));
+                }
+                const FF l = ff_norm(ledger);
+                *reinterpret_cast<float2*>(&nd.f0()) = make_float2(l.hi, l.lo);
+            } else {
+                for (int i = 1; i < 9; ++i) {
+                    const Real wr = (Real)w_of(i) * r;
+                    nd.f(i) = Codec::enc_f((Real)f[i * n + o], wr, (Real)1 / wr);
+                }
+                *reinterpret_cast<double*>(&nd.f0()) = f[o];
+            }
+        }
+        if (g) {
+            for (int i = 0; i < 9; ++i) {
+                const Real wr = (Real)w_of(i) * r;
+                nd.g(i) = Codec::enc_g((Real)g[i * n + o], wr, (Real)1 / wr);
+            }
         }
     }
     if (aux) {

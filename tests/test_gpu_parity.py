@@ -272,6 +272,29 @@ def test_mixed_precision_static_drop(prec, phi_tol):
         assert abs(d["dp"] - lap) / lap < 0.01, (d["dp"], lap)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "mix_fp16", "mix_bf16"])
+@pytest.mark.parametrize("case", ["static_drop", "thread"])
+def test_population_sum_is_conserved_by_the_ledger(prec, case):
+    """The step conserves the sum of all populations (sum r phi, Eq. 16):
+    in 16-bit storage exactly (every value the f_0 ledger adds lies on its
+    column grid, so its FP32 sums are exact: the exact sums of the stored
+    state before and after 500 steps are equal bit for bit), in FP32 to the
+    double-float ledger's ~2^-48.  z walls and axis (static drop), periodic z
+    (thread)."""
+    c = dict(W.static_drop() if case == "static_drop" else W.thread_breakup(), precision=prec)
+    sim = run_gpu(c, 0)
+    total0 = math.fsum(sim.state()[0].ravel())
+    sim.step(500)
+    total = math.fsum(sim.state()[0].ravel())
+    assert sim.diagnostics()["nonfinite"] == 0
+    sim.close()
+    print(prec, case, "sum of populations", total0, total, (total - total0) / total0)
+    if prec == "fp32":
+        assert abs(total - total0) <= 1e-13 * total0
+    else:
+        assert total == total0
+
+
 def test_diagnostics_leave_out_nonfinite_nodes_like_the_oracle():
     """One NaN in phi0 reaches u and p of its 16 stencil neighbours (Eq. 39-40).
     The GPU record and the oracle record both count those 17 nodes and leave
