@@ -35,17 +35,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS and % HBM roofline: FP64/FP32 vs mixed-precision/batched at stated error"
 # Algorithmic bytes per node update (populations read + written, f_0 -- FP64,
-# the FP32 ledger pair, or the 16-bit forms' single FP32 ledger value --,
+# the double-float ledger of FP32 and bfloat16, or FP16's single FP32 word --,
 # chi^{n-1} read + written; the lagged-p array is not touched).
 BYTES_PER_NODE = {
     "fp64": 2 * (9 * 8 + 9 * 8 + 2 * 8),       # 320
     "fp32": 2 * (8 + 8 * 4 + 9 * 4 + 2 * 4),    # 168
     "mix_fp16": 2 * (4 + 8 * 2 + 9 * 2 + 2 * 4),  # 92
-    "mix_bf16": 2 * (4 + 8 * 2 + 9 * 2 + 2 * 4),  # 92
+    "mix_bf16": 2 * (8 + 8 * 2 + 9 * 2 + 2 * 4),  # 100
 }
 # The wider per-node byte count that also charges the p^{n-1} plane (read and
 # written; FP64 also phi once each way); reported beside the count above.
-BYTES_PER_NODE_WITH_P = {"fp64": 352, "fp32": 176, "mix_fp16": 100, "mix_bf16": 100}
+BYTES_PER_NODE_WITH_P = {"fp64": 352, "fp32": 176, "mix_fp16": 100, "mix_bf16": 108}
 DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf16": "f32 (bf16 storage)"}
 # DRAM bytes per node update of the step kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the nodes of the captured

@@ -25,8 +25,8 @@ constexpr int kGraphSteps = 32;  // steps per captured graph (even: parity retur
 constexpr int kMax16BitNr = 65536;  // largest nr of the 16-bit storage forms
 
 size_t pt_size(int prec) { return prec == LBM_FP64 ? 8 : (prec == LBM_FP32 ? 4 : 2); }
-// f_0: FP64, the FP32 ledger pair, or the 16-bit forms' one FP32 ledger value
-size_t f0_size(int prec) { return prec == LBM_MIX_FP16 || prec == LBM_MIX_BF16 ? 4 : 8; }
+// f_0: FP64, the double-float ledger (FP32, bfloat16), or FP16's one exact FP32 ledger word
+size_t f0_size(int prec) { return prec == LBM_MIX_FP16 ? 4 : 8; }
 size_t real_size(int prec) { return prec == LBM_FP64 ? 8 : 4; }
 // bytes of one storage block (32 nodes) in this precision
 size_t block_bytes(int prec) {

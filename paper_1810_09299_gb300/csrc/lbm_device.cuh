@@ -116,6 +116,7 @@ struct CodecF64 {
     using PT = double;
     using F0T = double;
     static constexpr bool kLedger = false;
+    static constexpr bool kExactLedger = false;
     static constexpr bool kGrid = false;
     static constexpr bool kStreamStores = false;
     using PT2 = double2;  // (f_i, g_i) of one direction, stored together
@@ -132,6 +133,7 @@ struct CodecF32 {
     using F0T = float2;
     using PT2 = float2;
     static constexpr bool kLedger = true;
+    static constexpr bool kExactLedger = false;
     static constexpr bool kGrid = false;
     static constexpr bool kStreamStores = false;
     __device__ static Real dec_f(PT v, Real) { return v; }
@@ -170,12 +172,11 @@ __device__ __forceinline__ float fma_h(__nv_bfloat16 a, uint16_t b, float c) {
 // kStreamStores: the step writes its pushed populations with evict-first
 // stores (measured: -1.5 % on the 16-bit step, +2.8 % on the FP32 one).
 //
-// 16-bit storage on a grid.  Column j (r = j + 1/2) has the scales S_i of its
+// FP16 storage on a grid.  Column j (r = j + 1/2) has the scales S_i of its
 // directions: S_a = w_1 r = r / 9 rounded up to kScaleBits significant bits,
 // S_i = S_a for i = 1..4, S_a / 4 for i = 5..8, 4 S_a for i = 0 (the weights'
-// ratios), so S_i = w_i r / alpha with alpha in (2/3, 1] (FP16: 2 bits) or
-// (0.98, 1] (bfloat16: 7 bits).  f_i (i = 1..8) is stored as the centred
-// deviation
+// ratios), so S_i = w_i r / alpha with alpha in (2/3, 1] at 2 bits.  f_i
+// (i = 1..8) is stored as the centred deviation
 //   h_i = f_i / S_i - 1/2,
 // first rounded to a multiple of 2^-kGridExp, then to the 16-bit format
 // (which keeps it on that grid), and decoded as
@@ -190,8 +191,8 @@ __device__ __forceinline__ float fma_h(__nv_bfloat16 a, uint16_t b, float c) {
 // about 2, so plain FP32 additions of them are exact: f_0 is one FP32 value,
 // (sum of the incoming populations) minus (the stored outgoing f_1..8), and the
 // step conserves the sum of all populations exactly.
-// g_i is stored as kGScale g_i / S_i (FP16: the scale keeps typical values out
-// of the subnormal range; bfloat16 has FP32's range and takes no scale).
+// g_i is stored as kGScale g_i / S_i (the scale keeps typical values out of
+// FP16's subnormal range).
 __device__ __forceinline__ uint16_t bits16(__half v) { return __half_as_ushort(v); }
 __device__ __forceinline__ uint16_t bits16(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
 template <typename PT>
@@ -205,15 +206,15 @@ __device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float v) { return _
 // diagonal class (5..8); S16: S of both classes as 16-bit numbers (axis low),
 // S16g: the g decode scales S / kGScale of both classes, S16g0: that of g_0.
 struct GridCol {
-    float invS_a, G_a, cS_a, S_a;  // 1 / S, kGScale / S, S / 2; S_a
-    float invS_d, G_d, cS_d, pad0;
-    uint32_t S16, S16g, S16g0, pad1;
+    float invS_a, G_a, cS_a, S_a;  // 1 / S, kGScale / S, S / 2, S
+    float invS_d, G_d, cS_d, S_d;
+    uint32_t S16, S16g, S16g0, pad;
 };
 
 // S_a of column j
 template <class Codec>
 __device__ __forceinline__ float grid_sa(int j) {
-    constexpr uint32_t mask = (1u << (24 - Codec::kScaleBits)) - 1u;
+    constexpr uint32_t mask = (1u << (24 - Codec::kScaleBits)) - 1u;  // 0 at 24 bits
     const uint32_t u = __float_as_uint(__fmul_rn((float)j + 0.5f, 1.0f / 9.0f));
     return __uint_as_float((u + mask) & ~mask);
 }
@@ -232,11 +233,11 @@ __device__ __forceinline__ GridCol grid_col(int j) {
     g.cS_a = 0.5f * Sa;
     g.cS_d = 0.5f * Sd;
     g.S_a = Sa;
-    g.pad0 = 0.0f;
+    g.S_d = Sd;
     g.S16 = (uint32_t)bits16(to16<PT>(Sa)) | ((uint32_t)bits16(to16<PT>(Sd)) << 16);
     g.S16g = (uint32_t)bits16(to16<PT>(Sa / gs)) | ((uint32_t)bits16(to16<PT>(Sd / gs)) << 16);
     g.S16g0 = (uint32_t)bits16(to16<PT>(S0 / gs));
-    g.pad1 = 0u;
+    g.pad = 0u;
     return g;
 }
 
@@ -257,7 +258,8 @@ struct CodecGrid16 {
     using F0T = float;
     using PT2 = PT2_;
     static constexpr bool kLedger = false;
-    static constexpr bool kGrid = true;
+    static constexpr bool kExactLedger = true;  // one FP32 word, exact sums on the grid
+    static constexpr bool kGrid = true;         // column constants (GridCol)
     static constexpr bool kStreamStores = true;
     static constexpr float kGScale = (float)kGS;
     static constexpr int kGridExp = kE, kScaleBits = kBits;
@@ -290,23 +292,58 @@ struct CodecGrid16 {
     // g_0 (S_0 = 4 S_a)
     __device__ static PT enc_g0(float gv, const GridCol& g) { return to16<PT>(gv * (0.25f * g.G_a)); }
 };
-// (kGridExp, kScaleBits): measured on the 64 x 128 static drop against the
-// FP64 oracle (2000 steps, phi max / L2): FP16 (12, 4) 3.4e-2 / 7.2e-4,
-// (13, 3) 4.0e-2 / 8.3e-4, (14, 2) 1.7e-2 / 3.5e-4 (the finer grid matters
-// more than alpha near 1); bfloat16 (9, 7) 0.17 / 4.8e-3, (10, 6) 0.10 /
-// 3.3e-3, (11, 5) 0.11 / 2.3e-3, but with (11, 5) the ratio-1000 thread
-// (R0 = 20, k = 0.7) did not pinch off within 30,000 steps and the P2 drop's
-// frequency moved 8.7 % from the FP64 run's, against 2.3 % with (9, 7).
+// (kGridExp, kScaleBits) of FP16, measured on the 64 x 128 static drop
+// against the FP64 oracle (2000 steps, phi max / L2): (12, 4) 3.4e-2 /
+// 7.2e-4, (13, 3) 4.0e-2 / 8.3e-4, (14, 2) 1.7e-2 / 3.5e-4 (the finer grid
+// matters more than alpha near 1).
 #ifndef AXILBM_H16_E
 #define AXILBM_H16_E 14
 #define AXILBM_H16_B 2
 #endif
-#ifndef AXILBM_B16_E
-#define AXILBM_B16_E 9
-#define AXILBM_B16_B 7
-#endif
 using CodecH16 = CodecGrid16<__half, __half2, 256, AXILBM_H16_E, AXILBM_H16_B>;
-using CodecB16 = CodecGrid16<__nv_bfloat16, __nv_bfloat162, 1, AXILBM_B16_E, AXILBM_B16_B>;
+
+// bfloat16 storage keeps the centred deviation on the full FP32 scale w_i r:
+// f_i / (w_i r) - 1/2 and g_i / (w_i r), decoded as h wr + wr/2 in one
+// explicit FMA (wr/2 is exact), the same expression for the writer's mass
+// ledger and for the next reader, so both round alike; f_0 is the
+// double-float ledger of the FP32 codec.  bfloat16 keeps 8 significant bits,
+// so any scale short enough for the grid's exact decode leaves alpha = w r / S
+// a few of its units off 1, and a column's liquid deviations all round the
+// same way.  On grids of (9, 7), (10, 6) and (11, 5) bits the 256 x 1024
+// rising bubble at ratio 1000 went non-finite between 17,500 and 25,000
+// steps; this form follows it through 25,000 steps.
+struct CodecB16 {
+    using Real = float;
+    using PT = __nv_bfloat16;
+    using F0T = float2;
+    using PT2 = __nv_bfloat162;
+    static constexpr bool kLedger = true;
+    static constexpr bool kExactLedger = false;
+    static constexpr bool kGrid = false;
+    static constexpr bool kStreamStores = true;
+    __device__ static Real dec_f(PT v, Real wr) { return __fmaf_rn(__bfloat162float(v), wr, 0.5f * wr); }
+    __device__ static PT enc_f(Real v, Real, Real inv_wr) { return __float2bfloat16_rn(v * inv_wr - 0.5f); }
+    __device__ static Real dec_g(PT v, Real wr) { return __bfloat162float(v) * wr; }
+    __device__ static PT enc_g(Real v, Real, Real inv_wr) { return __float2bfloat16_rn(v * inv_wr); }
+    __device__ static PT2 enc_pair(Real f, Real g, Real, Real inv_wr) {
+        return __floats2bfloat162_rn(f * inv_wr - 0.5f, g * inv_wr);
+    }
+};
+
+// phi of a bfloat16 node (Eq. 16) from its raw stored f_0 and f_1..8: with
+// the decode f_i = (h_i + 1/2) w_i r the sum f_i / r reads
+//   phi = f_0 / r + (h_1 + .. + h_4 + 2) / 9 + (h_5 + .. + h_8 + 2) / 36,
+// summed from the stored values with eight mixed-precision adds (no decode);
+// every path that forms phi of such a node uses this one form.
+template <typename PT>
+__device__ __forceinline__ float phi_from_halves(float f0, const PT* h, float inv_r) {
+    float a = 2.0f, b = 2.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a = add_h(h[i], a);
+#pragma unroll
+    for (int i = 4; i < 8; ++i) b = add_h(h[i], b);
+    return __fmaf_rn(f0, inv_r, __fmaf_rn(a, 1.0f / 9.0f, b * (1.0f / 36.0f)));
+}
 
 // phi of a 16-bit node (Eq. 16) from its stored f_0 and h_1..8:
 //   sum f_i / r = (f_0 + S_a (A + B / 4)) / r,  A = 2 + h_1 + .. + h_4,
@@ -457,15 +494,17 @@ __device__ __forceinline__ int ghost_z(int k, int nz, int zper) {
 }
 
 // phi of a node from its raw stored f_0 (F0T) and f_1..8 (Eq. 16): the
-// plain sum in FP64 and FP32 storage, phi_grid in 16-bit storage (Sa: S_a of
-// the node's column; unused otherwise).
+// plain sum in FP64 and FP32 storage, phi_grid in FP16 storage (Sa: S_a of
+// the node's column; unused otherwise), phi_from_halves in bfloat16 storage.
 template <class Codec>
 __device__ __forceinline__ typename Codec::Real phi_of(const typename Codec::F0T& f0raw,
                                                         const typename Codec::PT* fraw,
                                                         typename Codec::Real inv_r, float Sa = 0.0f) {
     using Real = typename Codec::Real;
     if constexpr (Codec::kGrid) {
-        return phi_grid(f0raw, fraw, inv_r, Sa);
+        return phi_grid(f0_value(f0raw), fraw, inv_r, Sa);
+    } else if constexpr (sizeof(typename Codec::PT) == 2) {
+        return phi_from_halves(f0_value(f0raw), fraw, inv_r);
     } else {
         Real s = (Real)f0_value(f0raw);
 #pragma unroll
@@ -480,11 +519,11 @@ template <class Codec>
 __device__ __forceinline__ typename Codec::Real node_phi(const Node<Codec>& n, typename Codec::Real inv_r,
                                                           float Sa = 0.0f) {
     using Real = typename Codec::Real;
-    if constexpr (Codec::kGrid) {
+    if constexpr (sizeof(typename Codec::PT) == 2) {
         typename Codec::PT fraw[8];
 #pragma unroll
         for (int i = 1; i < 9; ++i) fraw[i - 1] = n.f(i);
-        return phi_grid(n.f0(), fraw, inv_r, Sa);
+        return phi_of<Codec>(n.f0(), fraw, inv_r, Sa);
     } else {
         Real s = (Real)f0_value(n.f0());
 #pragma unroll

@@ -22,7 +22,7 @@ constexpr int kPrefetchQuarters = 4;
 // consecutive columns are conflict-free 16-byte loads.
 struct GridTab {
     float4* A;  // invS_a, G_a, cS_a, S_a
-    float4* D;  // invS_d, G_d, cS_d, -
+    float4* D;  // invS_d, G_d, cS_d, S_d
     uint4* H;   // S16, S16g, S16g0, -
     __device__ __forceinline__ GridCol col(int b) const {
         const float4 a = A[b], d = D[b];
@@ -31,8 +31,8 @@ struct GridTab {
     }
     __device__ __forceinline__ void put(int b, const GridCol& g) const {
         A[b] = make_float4(g.invS_a, g.G_a, g.cS_a, g.S_a);
-        D[b] = make_float4(g.invS_d, g.G_d, g.cS_d, g.pad0);
-        H[b] = make_uint4(g.S16, g.S16g, g.S16g0, g.pad1);
+        D[b] = make_float4(g.invS_d, g.G_d, g.cS_d, g.S_d);
+        H[b] = make_uint4(g.S16, g.S16g, g.S16g0, g.pad);
     }
 };
 template <class Codec>
@@ -112,8 +112,9 @@ __device__ __forceinline__ void ring_cell(int q, int& a, int& b) {
 // rows (40 warps per SM, 48 registers a thread, a few bytes of spill): against
 // 4 CTAs (64 registers, no spill) that measured -3.4 % in FP32, -2.2 % in
 // FP16 and -5.1 % in BF16 storage with the paper's collision, with the same
-// results.  The raw-moment collision in 16-bit storage spills more at 48
-// registers and keeps 4 CTAs (0.772 against 0.817 ms).  General rates: 4 CTAs
+// results.  The raw-moment collision in bfloat16 storage spills more at 48
+// registers and keeps 4 CTAs (0.772 against 0.817 ms); with FP16's grid
+// codec it takes 5 (0.778 against 0.802 ms).  General rates: 4 CTAs
 // of 8 rows (64 registers, a few bytes of spill): on the 512-case batch with
 // every rate equal, -10.6 % in FP32 and -8.6 % in FP16 storage against 3 CTAs
 // at 80 registers.  AXILBM_GENERAL_CTAS overrides the count when building for
@@ -121,13 +122,18 @@ __device__ __forceinline__ void ring_cell(int q, int& a, int& b) {
 #ifndef AXILBM_GENERAL_CTAS
 #define AXILBM_GENERAL_CTAS 4
 #endif
+// AXILBM_STEP16_CTAS, AXILBM_RAW16_CTAS: the same counts for the 16-bit
+// kernels (the raw-moment one with FP16's grid codec), for tuning builds.
 #ifndef AXILBM_STEP16_CTAS
 #define AXILBM_STEP16_CTAS 5
+#endif
+#ifndef AXILBM_RAW16_CTAS
+#define AXILBM_RAW16_CTAS 5
 #endif
 template <class Codec, int BZ, int RM>
 constexpr int step_min_blocks() {
     constexpr int bz8 = (RM == kRatesPaperRaw && sizeof(typename Codec::PT) == 2)
-                            ? 4
+                            ? (Codec::kGrid ? AXILBM_RAW16_CTAS : 4)
                             : (sizeof(typename Codec::PT) == 2 ? AXILBM_STEP16_CTAS : 5);
     return sizeof(typename Codec::Real) == 8 ? 1
            : RM != kRatesGeneral ? (BZ >= 16 ? 2 : (BZ >= 8 ? bz8 : 8))
@@ -328,7 +334,7 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
 #pragma unroll
         for (int i = 1; i < 5; ++i) {
             if constexpr (Codec::kLedger) ff2_sub(ledger, make_float2((float)fs[i], (float)fs[i + 4]));
-            if constexpr (Codec::kGrid)
+            if constexpr (Codec::kExactLedger)
                 out_acc = i == 1 ? make_float2(fs[i], fs[i + 4]) : p_add(out_acc, make_float2(fs[i], fs[i + 4]));
         }
     } else {
@@ -344,7 +350,7 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     {                                                                                                    \
         const Real fa = AXILBM_STORE(I), fb = AXILBM_STORE(I + 4);                                       \
         if constexpr (Codec::kLedger) ff2_sub(ledger, make_float2((float)fa, (float)fb));                \
-        if constexpr (Codec::kGrid) out_acc = (I) == 1 ? make_float2(fa, fb) : p_add(out_acc, make_float2(fa, fb)); \
+        if constexpr (Codec::kExactLedger) out_acc = (I) == 1 ? make_float2(fa, fb) : p_add(out_acc, make_float2(fa, fb)); \
     }
         AXILBM_STORE_TWO(1)
         AXILBM_STORE_TWO(2)
@@ -364,7 +370,7 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     }
     // f_0: the collision's value (FP64), or the mass ledger: incoming total
     // minus the outgoing f_1..8 as they will be read back
-    if constexpr (Codec::kGrid) {
+    if constexpr (Codec::kExactLedger) {
         own.f0() = __fsub_rn(mf[0], __fadd_rn(out_acc.x, out_acc.y));
     } else if constexpr (Codec::kLedger) {
         const FF l = ff2_merge(ledger);
@@ -469,7 +475,7 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
         const Real inv_r = kInvrTable ? s_invr[bo] : rcp_(r);
         if constexpr (kG) {
             const GridCol g = T.col(bo);
-            f[0] = f0raw;
+            f[0] = f0_value(f0raw);
 #pragma unroll
             for (int i = 1; i < 9; ++i) f[i] = Codec::dec_f(fraw[i - 1], g, i > 4);
             sphi[(threadIdx.y + 2) * LD + bo] = phi_of<Codec>(f0raw, fraw, inv_r, g.S_a);
@@ -481,7 +487,8 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
                 f[i] = Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
                 sum += f[i];
             }
-            sphi[(threadIdx.y + 2) * LD + bo] = sum * inv_r;
+            // bfloat16: phi in the one form of phi_of (sum unused)
+            sphi[(threadIdx.y + 2) * LD + bo] = kKeepF ? phi_of<Codec>(f0raw, fraw, inv_r) : sum * inv_r;
         }
     } else {
         sphi[(threadIdx.y + 2) * LD + bo] = window_phi<Codec>(C, V, t, threadIdx.y + 2, bo, kG ? &T : nullptr);
@@ -591,6 +598,8 @@ step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
         if (in[p]) {
             if constexpr (kG) {
                 sphi[a * LD + bo] = phi_of<Codec>(f0raw[p], fraw[p], rcp_(r), T.A[bo].w);
+            } else if constexpr (sizeof(PT) == 2) {
+                sphi[a * LD + bo] = phi_of<Codec>(f0raw[p], fraw[p], rcp_(r));
             } else {
                 Real sum = (Real)f0_value(f0raw[p]);
 #pragma unroll
@@ -788,7 +797,7 @@ step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
         if (inside) {
             if constexpr (Codec::kGrid) {
                 const GridCol g = grid_col<Codec>(j);
-                f[0] = f0raw;
+                f[0] = f0_value(f0raw);
 #pragma unroll
                 for (int i = 1; i < 9; ++i) f[i] = Codec::dec_f(fraw[i - 1], g, i > 4);
                 sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = phi_of<Codec>(f0raw, fraw, rcp_(r), g.S_a);
@@ -800,7 +809,8 @@ step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
                     f[i] = Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
                     sum += f[i];
                 }
-                sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] = sum * rcp_(r);
+                sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] =
+                    sizeof(PT) == 2 ? phi_of<Codec>(f0raw, fraw, rcp_(r)) : sum * rcp_(r);
             }
         } else {
             sphi[(threadIdx.y + 2) * LD + threadIdx.x + 2] =
@@ -815,7 +825,8 @@ step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
                                            graw, chz_prev, chr_prev, p_prev, nullptr, f, cols);
             } else {
                 node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw,
-                                           graw, chz_prev, chr_prev, p_prev, nullptr, nullptr, NoCols{});
+                                           graw, chz_prev, chr_prev, p_prev, nullptr,
+                                           sizeof(PT) == 2 ? f : nullptr, NoCols{});
             }
         }
         if (NS == 1) {

@@ -276,11 +276,11 @@ def test_mixed_precision_static_drop(prec, phi_tol):
 @pytest.mark.parametrize("case", ["static_drop", "thread"])
 def test_population_sum_is_conserved_by_the_ledger(prec, case):
     """The step conserves the sum of all populations (sum r phi, Eq. 16):
-    in 16-bit storage exactly (every value the f_0 ledger adds lies on its
+    in FP16 storage exactly (every value the f_0 ledger adds lies on its
     column grid, so its FP32 sums are exact: the exact sums of the stored
-    state before and after 500 steps are equal bit for bit), in FP32 to the
-    double-float ledger's ~2^-48.  z walls and axis (static drop), periodic z
-    (thread)."""
+    state before and after 500 steps are equal bit for bit), in FP32 and
+    bfloat16 storage to the double-float ledger's ~2^-48.  z walls and axis
+    (static drop), periodic z (thread)."""
     c = dict(W.static_drop() if case == "static_drop" else W.thread_breakup(), precision=prec)
     sim = run_gpu(c, 0)
     total0 = math.fsum(sim.state()[0].ravel())
@@ -289,10 +289,10 @@ def test_population_sum_is_conserved_by_the_ledger(prec, case):
     assert sim.diagnostics()["nonfinite"] == 0
     sim.close()
     print(prec, case, "sum of populations", total0, total, (total - total0) / total0)
-    if prec == "fp32":
-        assert abs(total - total0) <= 1e-13 * total0
-    else:
+    if prec == "mix_fp16":
         assert total == total0
+    else:
+        assert abs(total - total0) <= 1e-13 * total0
 
 
 def test_diagnostics_leave_out_nonfinite_nodes_like_the_oracle():
