@@ -293,9 +293,11 @@ struct CodecGrid16 {
     __device__ static PT enc_g0(float gv, const GridCol& g) { return to16<PT>(gv * (0.25f * g.G_a)); }
 };
 // (kGridExp, kScaleBits) of FP16, measured on the 64 x 128 static drop
-// against the FP64 oracle (2000 steps, phi max / L2): (12, 4) 3.4e-2 /
-// 7.2e-4, (13, 3) 4.0e-2 / 8.3e-4, (14, 2) 1.7e-2 / 3.5e-4 (the finer grid
-// matters more than alpha near 1).
+// against the FP64 oracle (2000 steps, phi max / L2; paper's collision, then
+// the raw-moment one): (12, 4) 3.4e-2 / 7.2e-4; (13, 3) 4.0e-2 / 8.3e-4 and
+// 4.8e-2 / 1.0e-3; (14, 2) 1.7e-2 / 3.5e-4 and 2.0e-2 / 4.3e-4; (15, 1)
+// 2.4e-2 / 5.1e-4 and 7.1e-3 / 1.6e-4.  (14, 2) is the one within both
+// collisions' bounds.
 #ifndef AXILBM_H16_E
 #define AXILBM_H16_E 14
 #define AXILBM_H16_B 2
