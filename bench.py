@@ -50,11 +50,11 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf
 # DRAM bytes per node update of the step kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the nodes of the captured
 # launch), keyed by precision, launch variant and collision basis:
-# profiles/step_kernel_fp32_batched64cases.md (variant 0) and
-# profiles/step_kernel_seq2_fp32_batched64cases.md (variant 5, re-captured on
-# the current build).  Scaled to a
-# full launch by the node count.  Kept only for the kernel builds captured.
-TRAFFIC_B_PER_NODE = {("fp32", 0, "orthogonal"): 164.96, ("fp32", 5, "orthogonal"): 164.16}
+# profiles/step_kernel_seq2_fp32_batched64cases.md (variant 5, the shape the
+# autotuner picks for FP32, re-captured on the current build).  Scaled to a
+# full launch by the node count.  Kept only for the kernel builds captured
+# (another variant reports null).
+TRAFFIC_B_PER_NODE = {("fp32", 5, "orthogonal"): 164.16}
 # The FP64 step is bound by the FP64 pipe, not by HBM: FP64-pipe thread
 # instructions (DADD + DFMA + DMUL) per node update from one ncu capture
 # (profiles/step_kernel_fp64_batched64cases.md), against the pipe's rate
