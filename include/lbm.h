@@ -301,8 +301,9 @@ int lbm_autotune(lbm_handle* h, int32_t reps, int32_t* chosen);
  *   0, 1, 2  one node per thread, tiles of 8, 16, 4 rows;
  *   3, 4     one node per thread, tiles of 8, 16 rows staged in shared memory
  *            by TMA copies (persistent, pipelined; needs the tensor maps);
- *   5, 6     two nodes of a column per thread, tiles of 16 and 8 rows
- *            (FP64 handles run the one-node kernel of the same tile height). */
+ *   5, 6     two nodes of a column per thread, tiles of 16 rows; 6 keeps the
+ *            second node's stored inputs in shared memory while the first is
+ *            updated (FP64 handles run the one-node kernel of 16 rows). */
 int lbm_set_variant(lbm_handle* h, int32_t variant);
 int32_t lbm_num_variants(void);
 

@@ -58,9 +58,10 @@ constexpr int kNumVariants = 7;
 // tile height along z of each step-kernel variant (tile width is one warp along r);
 // variants 3 and 4 stage the tile through shared memory with TMA tensor loads;
 // variants 5 and 6 update two nodes of a column per thread, one after the
-// other (CTAs of 8 and 4 warps), in FP32 arithmetic, and run the one-node
+// other (CTAs of 8 warps; 6 parks the second node's inputs in shared memory
+// while the first is updated), in FP32 arithmetic, and run the one-node
 // kernel of their tile height in FP64
-constexpr int kVariantTZ[kNumVariants] = {8, 16, 4, 8, 16, 16, 8};
+constexpr int kVariantTZ[kNumVariants] = {8, 16, 4, 8, 16, 16, 16};
 constexpr bool kVariantTMA[kNumVariants] = {false, false, false, true, true, false, false};
 // tensor maps per case and tile height: the case's blocks in buffer 0 and 1
 // with a box of the tile's rows plus two above and below (staging, [0], [1]),

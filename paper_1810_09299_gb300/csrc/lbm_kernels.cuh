@@ -512,22 +512,37 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
 // results are those of step_kernel.  Both nodes' loads are in flight before
 // the tile's barrier (twice the loads per thread), and the phi ring is shared
 // by twice the nodes.
+//
+// STASH: the second node's stored inputs wait in shared memory, not in
+// registers, while the first node is updated, so the kernel fits fewer
+// registers and more CTAs per SM (AXILBM_STASH_CTAS).
 #ifndef AXILBM_SEQ2_CTAS
 #define AXILBM_SEQ2_CTAS 3
 #endif
-template <class Codec, int BZ, int RM>
+#ifndef AXILBM_STASH_CTAS
+#define AXILBM_STASH_CTAS 4
+#endif
+template <class Codec, int BZ, int RM, bool STASH = false>
 constexpr int seq2_min_blocks() {
-    return sizeof(typename Codec::Real) == 8 ? 1 : (BZ >= 8 ? AXILBM_SEQ2_CTAS : 2 * AXILBM_SEQ2_CTAS);
+    return sizeof(typename Codec::Real) == 8
+               ? 1
+               : (STASH ? AXILBM_STASH_CTAS : (BZ >= 8 ? AXILBM_SEQ2_CTAS : 2 * AXILBM_SEQ2_CTAS));
 }
 
-template <class Codec, int BZ, int RM>
-__global__ void __launch_bounds__(kTR * BZ, (seq2_min_blocks<Codec, BZ, RM>()))
+template <class Codec, int BZ, int RM, bool STASH = false>
+__global__ void __launch_bounds__(kTR * BZ, (seq2_min_blocks<Codec, BZ, RM, STASH>()))
 step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles, StateDev<Codec> S,
                  const CUtensorMap* __restrict__ maps, int map_set, int parity, int ntiles, int ahead) {
     using Real = typename Codec::Real;
     using PT = typename Codec::PT;
+    using PT2 = typename Codec::PT2;
     using F0T = typename Codec::F0T;
     constexpr int TZ = 2 * BZ;
+    constexpr int NS = STASH ? kTR * BZ : 1;
+    __shared__ F0T st_f0[NS];
+    __shared__ PT2 st_pr[8][NS];
+    __shared__ PT st_g0[NS];
+    __shared__ Real st_chz[NS], st_chr[NS], st_p[NS];
     constexpr int LD = kTR + 4;
     constexpr int NRING = 4 * kTR + 4 * (TZ + 4);
     static_assert(NRING == (TZ + 4) * LD - TZ * kTR, "the ring is the window without the tile");
@@ -610,11 +625,46 @@ step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
             sphi[a * LD + bo] = window_phi<Codec>(C, V, t, a, bo, kG ? &T : nullptr);
         }
     }
+    if constexpr (STASH) {
+        // the second node's inputs to shared memory (one slot per thread)
+        const int q = threadIdx.y * kTR + threadIdx.x;
+        if (in[1]) {
+            st_f0[q] = f0raw[1];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                PT2 pr;
+                pr.x = fraw[1][i - 1];
+                pr.y = graw[1][i];
+                st_pr[i - 1][q] = pr;
+            }
+            st_g0[q] = graw[1][0];
+            st_chz[q] = chz_prev[1];
+            st_chr[q] = chr_prev[1];
+            st_p[q] = p_prev[1];
+        }
+    }
     __syncthreads();
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         if (!in[p]) continue;
         const int k = t.k0 + threadIdx.y + p * BZ;
+        if (STASH && p == 1) {
+            // reloaded only now: the compiler may not hoist these shared loads
+            // above the first node's update
+            asm volatile("" ::: "memory");
+            const int q = threadIdx.y * kTR + threadIdx.x;
+            f0raw[1] = st_f0[q];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const PT2 pr = st_pr[i - 1][q];
+                fraw[1][i - 1] = pr.x;
+                graw[1][i] = pr.y;
+            }
+            graw[1][0] = st_g0[q];
+            chz_prev[1] = st_chz[q];
+            chr_prev[1] = st_chr[q];
+            p_prev[1] = st_p[q];
+        }
         if constexpr (kG) {
             const TabCols cols{T, j == 0 ? bo : bo - 1, bo, j + 1 == C.nr ? bo : bo + 1};
             node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2 + p * BZ, bo, k, j, k * C.pitch + j, f0raw[p],
@@ -1142,11 +1192,12 @@ void launch_step_rates(int variant, int ntiles, cudaStream_t st, const CaseDev* 
             break;
         default:
             if constexpr (sizeof(typename Codec::Real) == 4)
-                step_kernel_seq2<Codec, 4, RM><<<ntiles, dim3(kTR, 4), 0, st>>>(
-                    cs, tiles, S, maps, 0, parity, ntiles, kPrefetchQuarters * sms * seq2_min_blocks<Codec, 4, RM>() / 4);
+                step_kernel_seq2<Codec, 8, RM, true><<<ntiles, dim3(kTR, 8), 0, st>>>(
+                    cs, tiles, S, maps, 1, parity, ntiles,
+                    kPrefetchQuarters * sms * seq2_min_blocks<Codec, 8, RM, true>() / 4);
             else
-                step_kernel<Codec, 8, RM><<<ntiles, dim3(kTR, 8), 0, st>>>(
-                    cs, tiles, S, maps, 0, parity, ntiles, kPrefetchQuarters * sms * step_min_blocks<Codec, 8, RM>() / 4);
+                step_kernel<Codec, 16, RM><<<ntiles, dim3(kTR, 16), 0, st>>>(
+                    cs, tiles, S, maps, 1, parity, ntiles, kPrefetchQuarters * sms * step_min_blocks<Codec, 16, RM>() / 4);
             break;
     }
 }
