@@ -79,7 +79,10 @@ def test_invalid_arguments_rejected_before_device_work(L):
     # nz * pitch (pitch = nr rounded up to 32) must stay below 2^31 node indices
     for kw in ({"nr": 1}, {"nz": 0}, {"rho_g": 0.0}, {"nu_l": -1.0}, {"W": 0.0}, {"mobility": 0.0},
                {"sigma": -0.1}, {"precision": 7}, {"p_coupling": 3}, {"collision": 2}, {"collision": -1},
-               {"nz": 1 << 16, "nr": (1 << 15) + 1}):
+               {"nz": 1 << 16, "nr": (1 << 15) + 1},
+               # 16-bit storage: the column scales must be FP16 numbers (nr <= 65536)
+               {"nz": 16, "nr": 65537, "precision": "mix_fp16"},
+               {"nz": 16, "nr": 65537, "precision": "mix_bf16"}):
         c = workloads.static_drop(nr=16, nz=16, R=4.0)
         c.update(kw)
         bad.append(c)
