@@ -56,15 +56,19 @@ typedef enum {
  *                 of r phi, Eq. 16) changes only by round-off of about 2^-48.
  *   LBM_MIX_FP16  populations f_1..8 and g_0..8 stored as FP16 deviations
  *                 f_i / S_i - 1/2 and 256 g_i / S_i, S_i = w_i r of the
- *                 storing node rounded up to 2 significant bits (FP16; 7 for
- *                 bfloat16) in the ratios of the weights, the f deviation on a
- *                 2^-14 grid (2^-9 for bfloat16); arithmetic in FP32;
- *                 reductions in FP64.  Every stored f_i then decodes exactly,
- *                 to a multiple of a per-column grid, so f_0, one FP32 number,
- *                 holds the node's mass ledger in exact FP32 arithmetic: the
- *                 step conserves the sum of all populations exactly.
- *                 nr <= 65536.
- *   LBM_MIX_BF16  as LBM_MIX_FP16 with bfloat16 storage (no g scale). */
+ *                 storing node rounded up to 2 significant bits in the ratios
+ *                 of the weights, the f deviation on a 2^-14 grid; arithmetic
+ *                 in FP32; reductions in FP64.  Every stored f_i then decodes
+ *                 exactly, to a multiple of a per-column grid, so f_0, one
+ *                 FP32 number, holds the node's mass ledger in exact FP32
+ *                 arithmetic: the step conserves the sum of all populations
+ *                 exactly.  nr <= 65536.
+ *   LBM_MIX_BF16  populations stored as bfloat16 deviations f_i / (w_i r) - 1/2
+ *                 and g_i / (w_i r) on the full FP32 scale w_i r; f_0 is the
+ *                 double-float ledger of LBM_FP32 (round-off of about 2^-48).
+ *                 nr <= 65536.  bfloat16 keeps 8 significant bits: slowly
+ *                 moving interfaces can pin where the per-step change is below
+ *                 that resolution. */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_MIX_FP16 = 2, LBM_MIX_BF16 = 3 } lbm_precision;
 
 /* Coupling of the pressure p and the radial velocity u_r (Eq. 32 uses p, Eq. 33
