@@ -13,8 +13,14 @@ namespace axilbm {
 constexpr int kTR = 32;  // tile width along r = one warp
 // L2 prefetch distance of the step in quarters of a resident wave of CTAs
 // (SMs x CTAs per SM).  Measured on the 512-case batch: anything from 3/4 to
-// 3/2 of a wave gives the same time, half a wave or two waves less.
-constexpr int kPrefetchQuarters = 4;
+// 3/2 of a wave gives the same time, half a wave or two waves less.  With
+// FP16's grid codec (ms per step, one node per thread): 2 quarters 0.751,
+// 4 0.723, 8 0.721, 16 0.755; FP32 (two nodes per thread) 0.731, 0.733,
+// 0.955, 0.972.  AXILBM_PREFETCH_QUARTERS overrides it for tuning builds.
+#ifndef AXILBM_PREFETCH_QUARTERS
+#define AXILBM_PREFETCH_QUARTERS 4
+#endif
+constexpr int kPrefetchQuarters = AXILBM_PREFETCH_QUARTERS;
 
 // Column constants of the 16-bit grid codecs (GridCol) for the window
 // columns b = 0 .. kTR + 3 of a tile (column ghost_r(j0 - 2 + b)), built
