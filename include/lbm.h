@@ -307,7 +307,10 @@ int lbm_autotune(lbm_handle* h, int32_t reps, int32_t* chosen);
  *            by TMA copies (persistent, pipelined; needs the tensor maps);
  *   5, 6     two nodes of a column per thread, tiles of 16 rows; 6 keeps the
  *            second node's stored inputs in shared memory while the first is
- *            updated (FP64 handles run the one-node kernel of 16 rows). */
+ *            updated (FP64 handles run the one-node kernel of 16 rows)
+ *   7        LBM_MIX_FP16: two nodes of a column per thread whose macroscopic
+ *            step and collisions run together in packed FP32x2 lanes; other
+ *            precisions run variant 5 here. */
 int lbm_set_variant(lbm_handle* h, int32_t variant);
 int32_t lbm_num_variants(void);
 

@@ -54,15 +54,17 @@ AXILBM_DECLARE(h16)
 AXILBM_DECLARE(b16)
 #undef AXILBM_DECLARE
 
-constexpr int kNumVariants = 7;
+constexpr int kNumVariants = 8;
 // tile height along z of each step-kernel variant (tile width is one warp along r);
 // variants 3 and 4 stage the tile through shared memory with TMA tensor loads;
 // variants 5 and 6 update two nodes of a column per thread, one after the
 // other (CTAs of 8 warps; 6 parks the second node's inputs in shared memory
 // while the first is updated), in FP32 arithmetic, and run the one-node
-// kernel of their tile height in FP64
-constexpr int kVariantTZ[kNumVariants] = {8, 16, 4, 8, 16, 16, 16};
-constexpr bool kVariantTMA[kNumVariants] = {false, false, false, true, true, false, false};
+// kernel of their tile height in FP64; variant 7 updates the two nodes
+// together in packed FP32x2 lanes (FP16 storage; the other precisions run
+// variant 5's kernel there)
+constexpr int kVariantTZ[kNumVariants] = {8, 16, 4, 8, 16, 16, 16, 16};
+constexpr bool kVariantTMA[kNumVariants] = {false, false, false, true, true, false, false, false};
 // tensor maps per case and tile height: the case's blocks in buffer 0 and 1
 // with a box of the tile's rows plus two above and below (staging, [0], [1]),
 // and with a box of the tile's rows only (L2 prefetch, [2], [3])

@@ -7,6 +7,7 @@
 
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
+#include "lbm_lane.cuh"
 
 namespace axilbm {
 
@@ -386,6 +387,95 @@ __device__ __forceinline__ void node_update(const CaseDev& C, const CaseView<Cod
     }
 }
 
+// The stores of one FP16 node after its collisions (step a10 with the grid
+// codec): chi^n and p^n, g_0, the eight pushed (f_i, g_i) pairs with the
+// boundary rules of node_update, and f_0 = M f's first moment (mf0, the
+// incoming total) minus the stored outgoing f_1..8, exact on the grid.
+template <class Codec, class Cols>
+__device__ __forceinline__ void node_post_grid(const CaseDev& C, const CaseView<Codec>& V, int k, int j, int loc,
+                                               const float* mpf, const float* mpg, float chz, float chr, float p,
+                                               float mf0, const Cols& cols) {
+    const Node<Codec> own = V.out_node(loc);
+    own.chz() = chz;
+    own.chr() = chr;
+    if (C.p_coupling == 1) own.p() = p;
+    float fp[9], gp[9];
+    inverse_moments_fg(mpf, mpg, fp, gp);
+    const bool axis = (j == 0), wall = (j + 1 == C.nr), zlo = (k == 0), zhi = (k + 1 == C.nz);
+    using PT2 = typename Codec::PT2;
+    constexpr int kB = Block<Codec>::bytes, kPS = (int)sizeof(PT2);
+    const int lane = loc & 31;
+    unsigned char* const q0 = V.out_pt(loc).q;  // the node's own pair pointer
+    const int row = (C.pitch >> 5) * kB;         // one z row of blocks
+    const int step_r = lane == 31 ? kB - 31 * kPS : kPS;
+    const int step_l = lane == 0 ? -(kB - 31 * kPS) : -kPS;
+    float2 out_acc;  // the stored outgoing f of direction pairs (i, i + 4)
+    if ((zlo || zhi) && !C.zper) {
+        float fs[9];
+#define AXILBM_PUSH(I)                                                                        \
+    {                                                                                         \
+        const Dest d = destination<I>(k, j, C.nr, C.nz, C.zper);                              \
+        fs[I] = store_pair_grid<Codec>(&V.out_pt(d.k * C.pitch + d.j).pair(d.dir), cols.get(d.j - j + 1), \
+                                       (I) > 4, fp[I], gp[I]);                                \
+    }
+        AXILBM_PUSH(1)
+        AXILBM_PUSH(2)
+        AXILBM_PUSH(3)
+        AXILBM_PUSH(4)
+        AXILBM_PUSH(5)
+        AXILBM_PUSH(6)
+        AXILBM_PUSH(7)
+        AXILBM_PUSH(8)
+#undef AXILBM_PUSH
+        out_acc = make_float2(fs[1], fs[5]);
+#pragma unroll
+        for (int i = 2; i < 5; ++i) out_acc = p_add(out_acc, make_float2(fs[i], fs[i + 4]));
+    } else {
+        const int rowp = zhi ? -(C.nz - 1) * row : row;
+        const int rowm = zlo ? (C.nz - 1) * row : -row;
+#define AXILBM_STORE(I)                                                                                    \
+    store_pair_grid<Codec>(reinterpret_cast<PT2*>(q0 + push_offset<Codec, I>(axis, wall, rowp, rowm, step_r, step_l)), \
+                           cols.get(cr_of(I) + 1), (I) > 4, fp[I], gp[I])
+#define AXILBM_STORE_TWO(I)                                                                          \
+    {                                                                                                \
+        const float fa = AXILBM_STORE(I), fb = AXILBM_STORE(I + 4);                                  \
+        out_acc = (I) == 1 ? make_float2(fa, fb) : p_add(out_acc, make_float2(fa, fb));              \
+    }
+        AXILBM_STORE_TWO(1)
+        AXILBM_STORE_TWO(2)
+        AXILBM_STORE_TWO(3)
+        AXILBM_STORE_TWO(4)
+#undef AXILBM_STORE_TWO
+#undef AXILBM_STORE
+    }
+    {
+        const typename Codec::PT e0 = Codec::enc_g0(gp[0], cols.get(1));
+        if constexpr (Codec::kStreamStores) __stcs(&own.g(0), e0);
+        else own.g(0) = e0;
+    }
+    own.f0() = __fsub_rn(mf0, __fadd_rn(out_acc.x, out_acc.y));
+}
+
+// node_update for the FP16 grid codec: the same steps, with the macroscopic
+// step and both collisions in the explicit operations of lbm_lane.cuh (one
+// lane), so the packed two-node kernel computes the same numbers.
+template <class Codec, int RM, int LD, class Cols>
+__device__ __forceinline__ void node_update_grid(const CaseDev& C, const CaseView<Codec>& V, const float* sphi, int a,
+                                                 int b, int k, int j, int loc, const typename Codec::F0T& f0raw,
+                                                 const typename Codec::PT* fraw, const typename Codec::PT* graw,
+                                                 float chz_prev, float chr_prev, float p_prev, const float* fdec,
+                                                 const Cols& cols) {
+    static_assert(Codec::kGrid, "the grid codec's update");
+    PreCollision<float> pre;
+    node_pre<Codec>(f0raw, fraw, graw, (float)j + 0.5f, pre, fdec, cols.get(1));
+    lane::Macro<float> m;
+    lane::node_macros<float, LD, RM, true>(C, sphi, a, b, j, pre.mg, pre.g0, p_prev, m);
+    float mpf[9], mpg[9], chz, chr;
+    lane::collide_f<float, RM>(C, m, pre.mf, chz_prev, chr_prev, chz, chr, mpf);
+    lane::collide_g<float, RM>(C, m, mpg);
+    node_post_grid<Codec>(C, V, k, j, loc, mpf, mpg, chz, chr, m.p, pre.mf[0], cols);
+}
+
 // One time step for every node of every tile in `tiles`: one CTA per tile of
 // BZ rows (z) x 32 columns (r), one node per thread.  Each thread first issues
 // the loads of its own node; the node's phi goes to the shared window straight
@@ -504,8 +594,8 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
 
     if constexpr (kG) {
         const TabCols cols{T, j == 0 ? bo : bo - 1, bo, j + 1 == C.nr ? bo : bo + 1};
-        node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2, bo, k, j, loc, f0raw, fraw, graw, chz_prev,
-                                   chr_prev, p_prev, nullptr, f, cols);
+        node_update_grid<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2, bo, k, j, loc, f0raw, fraw, graw, chz_prev,
+                                        chr_prev, p_prev, f, cols);
     } else {
         node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2, bo, k, j, loc, f0raw, fraw, graw, chz_prev,
                                    chr_prev, p_prev, kInvrTable ? s_invr : nullptr, kKeepF ? f : nullptr, NoCols{});
@@ -673,13 +763,143 @@ step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
         }
         if constexpr (kG) {
             const TabCols cols{T, j == 0 ? bo : bo - 1, bo, j + 1 == C.nr ? bo : bo + 1};
-            node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2 + p * BZ, bo, k, j, k * C.pitch + j, f0raw[p],
-                                       fraw[p], graw[p], chz_prev[p], chr_prev[p], p_prev[p], nullptr, nullptr, cols);
+            node_update_grid<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2 + p * BZ, bo, k, j, k * C.pitch + j,
+                                            f0raw[p], fraw[p], graw[p], chz_prev[p], chr_prev[p], p_prev[p],
+                                            nullptr, cols);
         } else {
             node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2 + p * BZ, bo, k, j, k * C.pitch + j, f0raw[p],
                                        fraw[p], graw[p], chz_prev[p], chr_prev[p], p_prev[p], nullptr, nullptr,
                                        NoCols{});
         }
+    }
+}
+
+// The FP16 step with two nodes per thread in packed lanes (launch variant 7):
+// thread (x, y) of an 8-warp CTA holds the nodes (k0 + y, j) and (k0 + y + 8,
+// j) of a 16-row tile, decodes and stores each on its own, and runs the
+// macroscopic step and both collisions once for both, in the float2 lanes of
+// lbm_lane.cuh (one packed instruction per operation pair; the column's r,
+// 1/r and case parameters shared).  The phi window is held as row pairs,
+// spair[a][b] = (phi of window row a, of window row a + 8), so each stencil
+// point of both nodes is one 8-byte shared load.  Every lane computes exactly
+// what node_update_grid computes.
+// 3 CTAs per SM (80 registers, 68 bytes of spill): 0.674 ms on the 512-case
+// batch, against 0.805 ms at 2 (no spill) and 0.802 ms at 4.
+#ifndef AXILBM_PACK2_CTAS
+#define AXILBM_PACK2_CTAS 3
+#endif
+
+template <class Codec, int RM>
+__global__ void __launch_bounds__(kTR * 8, AXILBM_PACK2_CTAS)
+step_kernel_pack2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles, StateDev<Codec> S,
+                  const CUtensorMap* __restrict__ maps, int map_set, int parity, int ntiles, int ahead) {
+    static_assert(Codec::kGrid, "the FP16 grid codec's packed step");
+    using PT = typename Codec::PT;
+    using F0T = typename Codec::F0T;
+    constexpr int BZ = 8, TZ = 2 * BZ, LD = kTR + 4, NP = BZ + 4;
+    constexpr int NRING = 4 * kTR + 4 * (TZ + 4);
+    __shared__ float2 spair[NP * LD];
+    __shared__ __align__(16) CaseDev sC;
+    __shared__ float4 sgA[LD], sgD[LD];
+    __shared__ uint4 sgH[LD];
+    const GridTab T{sgA, sgD, sgH};
+    const TileDev t = tiles[blockIdx.x];
+    const int q = threadIdx.y * kTR + threadIdx.x;
+    if (q < LD) grid_tab_fill<Codec>(T, q, t.j0, cases[t.c].nr);
+    if (maps != nullptr && q == 0 && (int)blockIdx.x + ahead < ntiles) {
+        const TileDev tp = tiles[blockIdx.x + ahead];
+        const CUtensorMap* M = maps + ((size_t)tp.c * 2 + map_set) * kMapsPerCase + 2 + parity;
+        tensormap_acquire(M);
+        tma_prefetch_4d(M, 0, 0, tp.j0 >> 5, tp.k0);
+    }
+    if (q < (int)(sizeof(CaseDev) / 4))
+        reinterpret_cast<int32_t*>(&sC)[q] = reinterpret_cast<const int32_t*>(cases + t.c)[q];
+    __syncthreads();
+    const CaseDev& C = sC;
+    const CaseView<Codec> V = case_view<Codec>(S, C);
+    const int j = t.j0 + threadIdx.x;
+    // 1. both nodes' own loads
+    F0T f0raw[2] = {};
+    PT fraw[2][8], graw[2][9];
+    float chz_prev[2] = {}, chr_prev[2] = {}, p_prev[2] = {};
+    bool in[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int k = t.k0 + threadIdx.y + p * BZ;
+        in[p] = (j < C.nr) && (k < C.nz);
+        if (in[p]) {
+            const Node<Codec> n = V.in_node(k * C.pitch + j);
+            f0raw[p] = n.f0();
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const typename Codec::PT2 pr = n.pair(i);
+                fraw[p][i - 1] = pr.x;
+                graw[p][i] = pr.y;
+            }
+            graw[p][0] = n.g(0);
+            chz_prev[p] = n.chz();
+            chr_prev[p] = n.chr();
+            if (C.p_coupling == 1) p_prev[p] = n.p();
+        }
+    }
+    // phi of window row a, column b into its row-pair slot(s)
+    auto put = [&](int a, int b, float v) {
+        if (a < NP) spair[a * LD + b].x = v;
+        if (a >= BZ) spair[(a - BZ) * LD + b].y = v;
+    };
+    // 2. the ring of the phi window
+    for (int qq = q; qq < NRING; qq += kTR * BZ) {
+        int a, b;
+        ring_cell<TZ>(qq, a, b);
+        put(a, b, window_phi<Codec>(C, V, t, a, b, &T));
+    }
+    // 3. both nodes' own phi, in the form of the one-node kernel
+    const float r = (float)j + 0.5f;
+    const int bo = threadIdx.x + 2;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int a = threadIdx.y + 2 + p * BZ;
+        put(a, bo, in[p] ? phi_of<Codec>(f0raw[p], fraw[p], rcp_(r), T.A[bo].w)
+                         : window_phi<Codec>(C, V, t, a, bo, &T));
+    }
+    __syncthreads();
+    if (!in[0]) return;  // the second node lies below the first
+    const TabCols cols{T, j == 0 ? bo : bo - 1, bo, j + 1 == C.nr ? bo : bo + 1};
+    // 4. decode and moments per node, then the macroscopic step and both
+    //    collisions once for both, in packed lanes
+    PreCollision<float> pre0, pre1;
+    node_pre<Codec>(f0raw[0], fraw[0], graw[0], r, pre0, nullptr, cols.get(1));
+    node_pre<Codec>(f0raw[1], fraw[1], graw[1], r, pre1, nullptr, cols.get(1));
+    float2 mf[9], mg[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        mf[i] = make_float2(pre0.mf[i], pre1.mf[i]);
+        mg[i] = make_float2(pre0.mg[i], pre1.mg[i]);
+    }
+    lane::Macro<float2> m;
+    lane::node_macros<float2, LD, RM, true>(C, spair, threadIdx.y + 2, bo, j, mg,
+                                            make_float2(pre0.g0, pre1.g0), make_float2(p_prev[0], p_prev[1]), m);
+    float2 mpf[9], mpg[9], chz, chr;
+    lane::collide_f<float2, RM>(C, m, mf, make_float2(chz_prev[0], chz_prev[1]),
+                                make_float2(chr_prev[0], chr_prev[1]), chz, chr, mpf);
+    lane::collide_g<float2, RM>(C, m, mpg);
+    // 5. the stores of each node
+    float mpf_n[9], mpg_n[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        mpf_n[i] = mpf[i].x;
+        mpg_n[i] = mpg[i].x;
+    }
+    const int k0 = t.k0 + threadIdx.y;
+    node_post_grid<Codec>(C, V, k0, j, k0 * C.pitch + j, mpf_n, mpg_n, chz.x, chr.x, m.p.x, pre0.mf[0], cols);
+    if (in[1]) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            mpf_n[i] = mpf[i].y;
+            mpg_n[i] = mpg[i].y;
+        }
+        const int k1 = k0 + BZ;
+        node_post_grid<Codec>(C, V, k1, j, k1 * C.pitch + j, mpf_n, mpg_n, chz.y, chr.y, m.p.y, pre1.mf[0], cols);
     }
 }
 
@@ -877,8 +1097,8 @@ step_kernel_pipe(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
             const int loc = k * C.pitch + j;
             if constexpr (Codec::kGrid) {
                 const CalcCols<Codec> cols{j == 0 ? j : j - 1, j, j + 1 == C.nr ? j : j + 1};
-                node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw,
-                                           graw, chz_prev, chr_prev, p_prev, nullptr, f, cols);
+                node_update_grid<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw,
+                                                fraw, graw, chz_prev, chr_prev, p_prev, f, cols);
             } else {
                 node_update<Codec, RM, LD>(C, V, sphi, threadIdx.y + 2, threadIdx.x + 2, k, j, loc, f0raw, fraw,
                                            graw, chz_prev, chr_prev, p_prev, nullptr,
@@ -1190,6 +1410,17 @@ void launch_step_rates(int variant, int ntiles, cudaStream_t st, const CaseDev* 
         case 4: launch_tma<Codec, 16, RM>(ntiles, st, cs, tiles, S, D, parity); break;
         case 5:
             if constexpr (sizeof(typename Codec::Real) == 4)
+                step_kernel_seq2<Codec, 8, RM><<<ntiles, dim3(kTR, 8), 0, st>>>(
+                    cs, tiles, S, maps, 1, parity, ntiles, kPrefetchQuarters * sms * seq2_min_blocks<Codec, 8, RM>() / 4);
+            else
+                step_kernel<Codec, 16, RM><<<ntiles, dim3(kTR, 16), 0, st>>>(
+                    cs, tiles, S, maps, 1, parity, ntiles, kPrefetchQuarters * sms * step_min_blocks<Codec, 16, RM>() / 4);
+            break;
+        case 7:
+            if constexpr (Codec::kGrid)
+                step_kernel_pack2<Codec, RM><<<ntiles, dim3(kTR, 8), 0, st>>>(
+                    cs, tiles, S, maps, 1, parity, ntiles, kPrefetchQuarters * sms * AXILBM_PACK2_CTAS / 4);
+            else if constexpr (sizeof(typename Codec::Real) == 4)
                 step_kernel_seq2<Codec, 8, RM><<<ntiles, dim3(kTR, 8), 0, st>>>(
                     cs, tiles, S, maps, 1, parity, ntiles, kPrefetchQuarters * sms * seq2_min_blocks<Codec, 8, RM>() / 4);
             else
