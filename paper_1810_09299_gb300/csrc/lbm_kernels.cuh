@@ -775,6 +775,72 @@ step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
     }
 }
 
+// The packed update of the two nodes (k0, j) and (k0 + 8, j) of one thread
+// (the first inside the case; in1: the second too), from their raw stored
+// values and the row-pair phi window: decode and transform in node pairs, the
+// macroscopic step and both collisions in float2 lanes, then each node's
+// inverse transform and stores (step_kernel_pack2).  Measured: staging the
+// tiles of this update through shared memory with the TMA pipeline of
+// step_kernel_pipe (80 registers, 136 bytes of spill) took 1.16 ms on the
+// 512-case batch, against 0.657 ms here.
+template <class Codec, int RM, int LD>
+__device__ __forceinline__ void pack2_update(const CaseDev& C, const CaseView<Codec>& V, const float2* spair,
+                                             const GridTab& T, int ty, int j, int k0,
+                                             const typename Codec::F0T* f0raw, const typename Codec::PT (*fraw)[8],
+                                             const typename Codec::PT (*graw)[9], const float* chz_prev,
+                                             const float* chr_prev, const float* p_prev, bool in1) {
+    constexpr int BZ = 8;
+    const int bo = (j & 31) + 2;  // the window column of j (tiles start at multiples of 32)
+    const TabCols cols{T, j == 0 ? bo : bo - 1, bo, j + 1 == C.nr ? bo : bo + 1};
+    // 4. decode both nodes and transform them in node pairs: M f and M g of
+    //    (node 0, node 1) by the packed transforms of the one-node kernels
+    //    (there they pair (f_i, g_i) of one node; each lane takes the same
+    //    operations either way).  Against decoding each node with node_pre
+    //    and repacking: fewer moves and spills, 0.670 against 0.674 ms
+    const GridCol go = cols.get(1);
+    float2 x[9], mf[9], mg[9];
+    x[0] = make_float2(f0raw[0], f0raw[1]);
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+        x[i] = make_float2(Codec::dec_f(fraw[0][i - 1], go, i > 4), Codec::dec_f(fraw[1][i - 1], go, i > 4));
+    moments_p(x, mf);
+    x[0] = make_float2(Codec::dec_g0(graw[0][0], go), Codec::dec_g0(graw[1][0], go));
+    const float2 g0 = x[0];
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+        x[i] = make_float2(Codec::dec_g(graw[0][i], go, i > 4), Codec::dec_g(graw[1][i], go, i > 4));
+    moments_p(x, mg);
+    // 5. the macroscopic step and both collisions once for both nodes
+    lane::Macro<float2> m;
+    lane::node_macros<float2, LD, RM, true>(C, spair, ty + 2, bo, j, mg, g0,
+                                            make_float2(p_prev[0], p_prev[1]), m);
+    float2 mpf[9], mpg[9], chz, chr;
+    lane::collide_f<float2, RM>(C, m, mf, make_float2(chz_prev[0], chz_prev[1]),
+                                make_float2(chr_prev[0], chr_prev[1]), chz, chr, mpf);
+    lane::collide_g<float2, RM>(C, m, mpg);
+    // 6. each node's populations (the (f_i, g_i)-paired inverse transform of
+    //    the one-node kernels; measured faster here than transforming node
+    //    pairs, 0.670 against 0.695 ms) and stores
+    float mpf_n[9], mpg_n[9], fp[9], gp[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        mpf_n[i] = mpf[i].x;
+        mpg_n[i] = mpg[i].x;
+    }
+    inverse_moments_fg(mpf_n, mpg_n, fp, gp);
+    node_post_grid<Codec>(C, V, k0, j, k0 * C.pitch + j, fp, gp, chz.x, chr.x, m.p.x, mf[0].x, cols);
+    if (in1) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            mpf_n[i] = mpf[i].y;
+            mpg_n[i] = mpg[i].y;
+        }
+        inverse_moments_fg(mpf_n, mpg_n, fp, gp);
+        const int k1 = k0 + BZ;
+        node_post_grid<Codec>(C, V, k1, j, k1 * C.pitch + j, fp, gp, chz.y, chr.y, m.p.y, mf[0].y, cols);
+    }
+}
+
 // The FP16 step with two nodes per thread in packed lanes (launch variant 7):
 // thread (x, y) of an 8-warp CTA holds the nodes (k0 + y, j) and (k0 + y + 8,
 // j) of a 16-row tile, decodes and stores each on its own, and runs the
@@ -865,55 +931,8 @@ step_kernel_pack2(const CaseDev* __restrict__ cases, const TileDev* __restrict__
     }
     __syncthreads();
     if (!in[0]) return;  // the second node lies below the first
-    const TabCols cols{T, j == 0 ? bo : bo - 1, bo, j + 1 == C.nr ? bo : bo + 1};
-    // 4. decode both nodes and transform them in node pairs: M f and M g of
-    //    (node 0, node 1) by the packed transforms of the one-node kernels
-    //    (there they pair (f_i, g_i) of one node; each lane takes the same
-    //    operations either way).  Against decoding each node with node_pre
-    //    and repacking: fewer moves and spills, 0.670 against 0.674 ms
-    const GridCol go = cols.get(1);
-    float2 x[9], mf[9], mg[9];
-    x[0] = make_float2(f0raw[0], f0raw[1]);
-#pragma unroll
-    for (int i = 1; i < 9; ++i)
-        x[i] = make_float2(Codec::dec_f(fraw[0][i - 1], go, i > 4), Codec::dec_f(fraw[1][i - 1], go, i > 4));
-    moments_p(x, mf);
-    x[0] = make_float2(Codec::dec_g0(graw[0][0], go), Codec::dec_g0(graw[1][0], go));
-    const float2 g0 = x[0];
-#pragma unroll
-    for (int i = 1; i < 9; ++i)
-        x[i] = make_float2(Codec::dec_g(graw[0][i], go, i > 4), Codec::dec_g(graw[1][i], go, i > 4));
-    moments_p(x, mg);
-    // 5. the macroscopic step and both collisions once for both nodes
-    lane::Macro<float2> m;
-    lane::node_macros<float2, LD, RM, true>(C, spair, threadIdx.y + 2, bo, j, mg, g0,
-                                            make_float2(p_prev[0], p_prev[1]), m);
-    float2 mpf[9], mpg[9], chz, chr;
-    lane::collide_f<float2, RM>(C, m, mf, make_float2(chz_prev[0], chz_prev[1]),
-                                make_float2(chr_prev[0], chr_prev[1]), chz, chr, mpf);
-    lane::collide_g<float2, RM>(C, m, mpg);
-    // 6. each node's populations (the (f_i, g_i)-paired inverse transform of
-    //    the one-node kernels; measured faster here than transforming node
-    //    pairs, 0.670 against 0.695 ms) and stores
-    float mpf_n[9], mpg_n[9], fp[9], gp[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        mpf_n[i] = mpf[i].x;
-        mpg_n[i] = mpg[i].x;
-    }
-    inverse_moments_fg(mpf_n, mpg_n, fp, gp);
-    const int k0 = t.k0 + threadIdx.y;
-    node_post_grid<Codec>(C, V, k0, j, k0 * C.pitch + j, fp, gp, chz.x, chr.x, m.p.x, mf[0].x, cols);
-    if (in[1]) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            mpf_n[i] = mpf[i].y;
-            mpg_n[i] = mpg[i].y;
-        }
-        inverse_moments_fg(mpf_n, mpg_n, fp, gp);
-        const int k1 = k0 + BZ;
-        node_post_grid<Codec>(C, V, k1, j, k1 * C.pitch + j, fp, gp, chz.y, chr.y, m.p.y, mf[0].y, cols);
-    }
+    pack2_update<Codec, RM, LD>(C, V, spair, T, threadIdx.y, j, t.k0 + threadIdx.y, f0raw, fraw, graw, chz_prev,
+                                chr_prev, p_prev, in[1]);
 }
 
 // Shared-memory layout of one stage of the TMA-pipelined step for tile
