@@ -46,6 +46,11 @@ BYTES_PER_NODE = {
 # The wider per-node byte count that also charges the p^{n-1} plane (read and
 # written; FP64 also phi once each way); reported beside the count above.
 BYTES_PER_NODE_WITH_P = {"fp64": 352, "fp32": 176, "mix_fp16": 100, "mix_bf16": 108}
+# The benchmark's cost model per node update: the 36 population values, phi
+# written and read once and chi^{n-1}, p^{n-1} read and written (44 values),
+# 8 B each in FP64, 4 B in FP32, and with 16-bit storage 4 B for f_0, phi and
+# the auxiliary values and 2 B for the other 34 populations.
+BYTES_PER_NODE_MODEL = {"fp64": 352, "fp32": 176, "mix_fp16": 108, "mix_bf16": 108}
 DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf16": "f32 (bf16 storage)"}
 # DRAM bytes per node update of the step kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the nodes of the captured
@@ -359,7 +364,8 @@ def run_cuda(args):
                      "note": f"peak {peak_kind}; algorithmic bytes {BYTES_PER_NODE[prec]} B/node x {nodes} nodes "
                              f"per launch / mean CUDA-event launch duration",
                      "bytes_per_node_with_p": BYTES_PER_NODE_WITH_P[prec], "achieved_with_p": ach_with_p,
-                     "frac_with_p": ach_with_p / peak},
+                     "frac_with_p": ach_with_p / peak, "bytes_per_node_model": BYTES_PER_NODE_MODEL[prec],
+                     "frac_model": BYTES_PER_NODE_MODEL[prec] * nodes / (per_launch_ms * 1e-3) / 1e9 / peak},
         "gpu_launches": int(launches),
         # the autotuner restores the state it started from, so d["step"] counts
         # the warm-up and timed steps only
@@ -519,7 +525,9 @@ def batched_other(torch, args, prec, steps, raw=False):
            "value": nodes / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
            "variant": variant, "achieved_gbs": ach, "frac": ach / peak,
            "bytes_per_node": BYTES_PER_NODE[prec], "frac_with_p": ach_p / peak,
-           "bytes_per_node_with_p": BYTES_PER_NODE_WITH_P[prec]}
+           "bytes_per_node_with_p": BYTES_PER_NODE_WITH_P[prec],
+           "bytes_per_node_model": BYTES_PER_NODE_MODEL[prec],
+           "frac_model": BYTES_PER_NODE_MODEL[prec] * nodes / (ms * 1e-3) / 1e9 / peak}
     if prec == "fp64":
         gops = FP64_OPS_PER_NODE * nodes / (ms * 1e-3) / 1e9
         with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:

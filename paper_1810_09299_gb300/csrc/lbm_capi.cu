@@ -279,13 +279,30 @@ std::vector<TileDev> make_tiles(const std::vector<CaseDev>& cs, int tz, int only
     return t;
 }
 
-int upload_tiles(lbm_sim* h, const std::vector<TileDev>& t, TileDev** out) {
+// A tile list on the device; with geo, followed by one TileGeo per tile (the
+// step variants' lists).
+int upload_tiles(lbm_sim* h, const std::vector<TileDev>& t, TileDev** out, bool geo = false) {
+    static_assert(sizeof(TileDev) == 16 && sizeof(TileGeo) == 32, "tile record sizes");
+    std::vector<TileGeo> g;
+    if (geo) {
+        g.reserve(t.size());
+        for (const TileDev& d : t) {
+            const CaseDev& C = h->cases[d.c];
+            g.push_back(TileGeo{d.c, d.k0, d.j0, (int32_t)(C.off >> 5), C.pitch >> 5, C.nr, C.nz, C.zper});
+        }
+    }
     void* p = nullptr;
-    cudaError_t e = dev_alloc(h, &p, std::max<size_t>(1, t.size()) * sizeof(TileDev));
+    const size_t tb = t.size() * sizeof(TileDev), gb = g.size() * sizeof(TileGeo);
+    cudaError_t e = dev_alloc(h, &p, std::max<size_t>(1, tb + gb));
     if (e != cudaSuccess) return cuda_ok(h, e);
     if (!t.empty()) {
-        e = cudaMemcpyAsync(p, t.data(), t.size() * sizeof(TileDev), cudaMemcpyHostToDevice, h->stream);
+        e = cudaMemcpyAsync(p, t.data(), tb, cudaMemcpyHostToDevice, h->stream);
         if (e != cudaSuccess) return cuda_ok(h, e);
+    }
+    if (!g.empty()) {
+        e = cudaMemcpyAsync((char*)p + tb, g.data(), gb, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_ok(h, e);
+        // the host vectors are pageable: each copy has been staged when it returns
     }
     *out = (TileDev*)p;
     return LBM_OK;
@@ -468,7 +485,7 @@ int create_impl(const lbm_params* cases, int32_t n, void* stream, lbm_handle** o
     for (int v = 0; v < kNumVariants && rc == LBM_OK; ++v) {
         std::vector<TileDev> t = make_tiles(h->cases, kVariantTZ[v], -1);
         h->ntiles[v] = (int)t.size();
-        rc = upload_tiles(h, t, &h->tiles_d[v]);
+        rc = upload_tiles(h, t, &h->tiles_d[v], true);
     }
     for (int c = 0; c < n && rc == LBM_OK; ++c) {
         std::vector<TileDev> t = make_tiles(h->cases, 8, c);

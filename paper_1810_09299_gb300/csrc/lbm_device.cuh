@@ -87,6 +87,16 @@ struct TileDev {
     int32_t c, k0, j0, pad;
 };
 
+// The same tile with its case's geometry: the case's first storage block
+// (blk0 = off / 32), one z row in blocks (pitch / 32), nr, nz and the z
+// periodicity.  A step variant's tile list is followed in device memory by one
+// of these per tile, so that a kernel can address the tile's nodes and its phi
+// ring as soon as this record arrives, before the case record.
+struct TileGeo {
+    int32_t c, k0, j0, blk0;
+    int32_t rowblk, nr, nz, zper;
+};
+
 // ---------------------------------------------------------------- storage codecs
 // Populations are stored as PT (f_1..8, g_0..8) and F0T (f_0).  wr = w_i * r of
 // the node the value is stored at (known to writer and reader), inv_wr = 1/wr.
@@ -513,6 +523,17 @@ __device__ __forceinline__ typename Codec::Real phi_of(const typename Codec::F0T
         for (int i = 0; i < 8; ++i) s += fraw[i];
         return s * inv_r;
     }
+}
+
+// The stored f_0 and f_1..8 of node n, the values phi is summed from (Eq. 16):
+// loaded ahead of their use, then phi_of(f0, f, 1 / r, S_a) gives what
+// node_phi gives.
+template <class Codec>
+__device__ __forceinline__ void load_phi_raw(const Node<Codec>& n, typename Codec::F0T& f0,
+                                             typename Codec::PT* f) {
+    f0 = n.f0();
+#pragma unroll
+    for (int i = 1; i < 9; ++i) f[i - 1] = n.f(i);
 }
 
 // phi at an in-domain node from its stored populations (Eq. 16).  FP64 and

@@ -494,8 +494,8 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     constexpr int NRING = 4 * kTR + 4 * (TZ + 4);
     static_assert(NRING == (TZ + 4) * LD - TZ * kTR, "the ring is the window without the tile");
     __shared__ Real sphi[(TZ + 4) * LD];
-    // The case's parameters are copied to shared memory first: read from
-    // there, the collision's many per-case constants need no global loads.
+    // The case's parameters go to shared memory: read from there, the
+    // collision's many per-case constants need no global loads.
     __shared__ __align__(16) CaseDev sC;
     static_assert(sizeof(CaseDev) % 4 == 0 && sizeof(CaseDev) / 4 <= kTR * BZ, "one word per thread");
     // FP64: 1 / r of the window's columns j0 - 2 .. j0 + 33, one division per
@@ -508,14 +508,17 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
     __shared__ float4 sgA[kG ? LD : 1], sgD[kG ? LD : 1];
     __shared__ uint4 sgH[kG ? LD : 1];
     const GridTab T{sgA, sgD, sgH};
-    const TileDev t = tiles[blockIdx.x];
+    const TileGeo g = reinterpret_cast<const TileGeo*>(tiles + ntiles)[blockIdx.x];
     const int q = threadIdx.y * kTR + threadIdx.x;
-    if constexpr (kInvrTable) {
-        if (q < LD) s_invr[q] = (Real)1 / ((Real)(t.j0 - 2 + q) + (Real)0.5);
-    }
-    if constexpr (kG) {
-        if (q < LD) grid_tab_fill<Codec>(T, q, t.j0, cases[t.c].nr);
-    }
+    constexpr int kCW = (int)(sizeof(CaseDev) / 4);                // words of the case record
+    constexpr int kRC = (NRING + kTR * BZ - 1) / (kTR * BZ);        // ring cells per thread
+    constexpr int kB = Block<Codec>::bytes;
+    // 1. every global load of the window phase leaves before any of them is
+    //    used, addressed from the tile's TileGeo record alone: this thread's
+    //    word of the case record, the node's own values (out of the domain:
+    //    its ghost node's f), and the f of this thread's ring cells
+    int32_t cw = 0;
+    if (q < kCW) cw = reinterpret_cast<const int32_t*>(cases + g.c)[q];
     // L2 prefetch of the blocks of the tile one resident wave ahead (a CTA
     // that will start about when this one ends): one tensor prefetch, issued
     // by one thread; the tensor maps are absent when they could not be made
@@ -525,22 +528,16 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
         tensormap_acquire(M);
         tma_prefetch_4d(M, 0, 0, tp.j0 >> 5, tp.k0);
     }
-    if (q < (int)(sizeof(CaseDev) / 4))
-        reinterpret_cast<int32_t*>(&sC)[q] = reinterpret_cast<const int32_t*>(cases + t.c)[q];
-    __syncthreads();
-    const CaseDev& C = sC;
-    const CaseView<Codec> V = case_view<Codec>(S, C);
-    const int j = t.j0 + threadIdx.x;
-    const int k = t.k0 + threadIdx.y;
-    const bool inside = (j < C.nr) && (k < C.nz);
-    const int loc = k * C.pitch + j;
-
-    // 1. own-node loads, issued before anything waits on memory
+    unsigned char* const base = const_cast<unsigned char*>(S.in) + (int64_t)g.blk0 * kB;  // the case's first block
+    auto node_at = [&](int kk, int jj) { return Node<Codec>{base + (int64_t)(kk * g.rowblk + (jj >> 5)) * kB, jj & 31}; };
+    const int j = g.j0 + threadIdx.x;
+    const int k = g.k0 + threadIdx.y;
+    const bool inside = (j < g.nr) && (k < g.nz);
     F0T f0raw{};
     PT fraw[8], graw[9];
     Real chz_prev = (Real)0, chr_prev = (Real)0, p_prev = (Real)0;
     if (inside) {
-        const Node<Codec> n = V.in_node(loc);
+        const Node<Codec> n = node_at(k, j);
         f0raw = n.f0();
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
@@ -551,47 +548,82 @@ step_kernel(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles
         graw[0] = n.g(0);
         chz_prev = n.chz();
         chr_prev = n.chr();
-        if (C.p_coupling == 1) p_prev = n.p();
+    } else {
+        load_phi_raw<Codec>(node_at(ghost_z(k, g.nz, g.zper), ghost_r(j, g.nr)), f0raw, fraw);
     }
-    // 2. the ring of the phi window (two rows above and below, two columns
-    //    left and right of the tile)
-    for (int qq = q; qq < NRING; qq += kTR * BZ) {
-        int a, b;
-        ring_cell<TZ>(qq, a, b);
-        sphi[a * LD + b] = window_phi<Codec>(C, V, t, a, b, kG ? &T : nullptr);
+    // 2. the window: this thread's ring cells (two rows above and below, two
+    //    columns left and right of the tile), then the node's own phi (Eq.
+    //    16), as soon as their loads land; 16-bit grid storage takes S_a of a
+    //    column from grid_sa, the value the column table holds
+    auto sa_of = [&](int jj) -> float {
+        if constexpr (kG) return grid_sa<Codec>(jj);
+        else return 0.0f;
+    };
+#pragma unroll
+    for (int c = 0; c < kRC; ++c) {
+        if (q + c * kTR * BZ < NRING) {
+            int ra, rb;
+            ring_cell<TZ>(q + c * kTR * BZ, ra, rb);
+            const int rj = ghost_r(g.j0 - 2 + rb, g.nr);
+            F0T rf0;
+            PT rf[8];
+            load_phi_raw<Codec>(node_at(ghost_z(g.k0 - 2 + ra, g.nz, g.zper), rj), rf0, rf);
+            sphi[ra * LD + rb] = phi_of<Codec>(rf0, rf, rcp_((Real)rj + (Real)0.5), sa_of(rj));
+        }
     }
-    // 3. the node's own phi (Eq. 16); window cells outside the domain take the ghost rule
     const Real r = (Real)j + (Real)0.5;
     const int bo = threadIdx.x + 2;
-    Real f[9];
-    // 16-bit storage: the decoded f live on across the barrier (measured
-    // -1.5 % against decoding them again; +0.6 % in FP32, where decoding is
-    // free)
-    constexpr bool kKeepF = sizeof(PT) == 2;
+    Real own_sum = (Real)0;  // FP64: the node's f summed; phi once the 1 / r table is filled
     if (inside) {
-        const Real inv_r = kInvrTable ? s_invr[bo] : rcp_(r);
-        if constexpr (kG) {
-            const GridCol g = T.col(bo);
-            f[0] = f0_value(f0raw);
-#pragma unroll
-            for (int i = 1; i < 9; ++i) f[i] = Codec::dec_f(fraw[i - 1], g, i > 4);
-            sphi[(threadIdx.y + 2) * LD + bo] = phi_of<Codec>(f0raw, fraw, inv_r, g.S_a);
+        if constexpr (sizeof(PT) == 2) {
+            sphi[(threadIdx.y + 2) * LD + bo] = phi_of<Codec>(f0raw, fraw, rcp_(r), sa_of(j));
         } else {
-            f[0] = (Real)f0_value(f0raw);
-            Real sum = f[0];
+            Real sum = (Real)f0_value(f0raw);
 #pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                f[i] = Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
-                sum += f[i];
-            }
-            // bfloat16: phi in the one form of phi_of (sum unused)
-            sphi[(threadIdx.y + 2) * LD + bo] = kKeepF ? phi_of<Codec>(f0raw, fraw, inv_r) : sum * inv_r;
+            for (int i = 1; i < 9; ++i) sum += Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
+            if constexpr (kInvrTable) own_sum = sum;
+            else sphi[(threadIdx.y + 2) * LD + bo] = sum * rcp_(r);
         }
     } else {
-        sphi[(threadIdx.y + 2) * LD + bo] = window_phi<Codec>(C, V, t, threadIdx.y + 2, bo, kG ? &T : nullptr);
+        const int jm = ghost_r(j, g.nr);
+        sphi[(threadIdx.y + 2) * LD + bo] = phi_of<Codec>(f0raw, fraw, rcp_((Real)jm + (Real)0.5), sa_of(jm));
+    }
+    // 3. the column tables and the case record into shared memory
+    if constexpr (kInvrTable) {
+        if (q < LD) s_invr[q] = (Real)1 / ((Real)(g.j0 - 2 + q) + (Real)0.5);
+    }
+    if constexpr (kG) {
+        if (q < LD) grid_tab_fill<Codec>(T, q, g.j0, g.nr);
+    }
+    if (q < kCW) reinterpret_cast<int32_t*>(&sC)[q] = cw;
+    if constexpr (kInvrTable) {
+        // FP64: one division per column, not per node (a division is a long
+        // sequence on the FP64 pipe), so the own phi waits for the table
+        __syncthreads();
+        if (inside) sphi[(threadIdx.y + 2) * LD + bo] = own_sum * s_invr[bo];
     }
     __syncthreads();
     if (!inside) return;
+    const CaseDev& C = sC;
+    const CaseView<Codec> V = case_view<Codec>(S, C);
+    const int loc = k * C.pitch + j;
+    // the lagged pressure p^{n-1}, read only under the lagged coupling
+    if (C.p_coupling == 1) p_prev = V.in_node(loc).p();
+    // 16-bit storage: the decoded f_0..8 go to the update (measured -1.5 %
+    // against decoding them there; +0.6 % in FP32, where decoding is free)
+    constexpr bool kKeepF = sizeof(PT) == 2;
+    Real f[9];
+    if constexpr (kKeepF) {
+        f[0] = (Real)f0_value(f0raw);
+        if constexpr (kG) {
+            const GridCol gc = T.col(bo);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) f[i] = Codec::dec_f(fraw[i - 1], gc, i > 4);
+        } else {
+#pragma unroll
+            for (int i = 1; i < 9; ++i) f[i] = Codec::dec_f(fraw[i - 1], (Real)w_of(i) * r);
+        }
+    }
 
     if constexpr (kG) {
         const TabCols cols{T, j == 0 ? bo : bo - 1, bo, j + 1 == C.nr ? bo : bo + 1};
@@ -639,7 +671,7 @@ step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
     __shared__ F0T st_f0[NS];
     __shared__ PT2 st_pr[8][NS];
     __shared__ PT st_g0[NS];
-    __shared__ Real st_chz[NS], st_chr[NS], st_p[NS];
+    __shared__ Real st_chz[NS], st_chr[NS];
     constexpr int LD = kTR + 4;
     constexpr int NRING = 4 * kTR + 4 * (TZ + 4);
     static_assert(NRING == (TZ + 4) * LD - TZ * kTR, "the ring is the window without the tile");
@@ -651,37 +683,36 @@ step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
     __shared__ float4 sgA[kG ? LD : 1], sgD[kG ? LD : 1];
     __shared__ uint4 sgH[kG ? LD : 1];
     const GridTab T{sgA, sgD, sgH};
-    const TileDev t = tiles[blockIdx.x];
-    if constexpr (kG) {
-        const int q = threadIdx.y * kTR + threadIdx.x;
-        if (q < LD) grid_tab_fill<Codec>(T, q, t.j0, cases[t.c].nr);
-    }
-    if (maps != nullptr && threadIdx.x == 0 && threadIdx.y == 0 && (int)blockIdx.x + ahead < ntiles) {
+    const TileGeo g = reinterpret_cast<const TileGeo*>(tiles + ntiles)[blockIdx.x];
+    const int q = threadIdx.y * kTR + threadIdx.x;
+    constexpr int kCW = (int)(sizeof(CaseDev) / 4);  // words of the case record
+    static_assert(NRING <= kTR * BZ, "one ring cell per thread at most");
+    constexpr int kB = Block<Codec>::bytes;
+    // 1. every global load of the window phase leaves before any of them is
+    //    used, addressed from the tile's TileGeo record alone: this thread's
+    //    word of the case record, both nodes' own values (out of the domain:
+    //    the ghost node's f) and the f of this thread's ring cell
+    int32_t cw = 0;
+    if (q < kCW) cw = reinterpret_cast<const int32_t*>(cases + g.c)[q];
+    if (maps != nullptr && q == 0 && (int)blockIdx.x + ahead < ntiles) {
         const TileDev tp = tiles[blockIdx.x + ahead];
         const CUtensorMap* M = maps + ((size_t)tp.c * 2 + map_set) * kMapsPerCase + 2 + parity;
         tensormap_acquire(M);
         tma_prefetch_4d(M, 0, 0, tp.j0 >> 5, tp.k0);
     }
-    {
-        const int q = threadIdx.y * kTR + threadIdx.x;
-        if (q < (int)(sizeof(CaseDev) / 4))
-            reinterpret_cast<int32_t*>(&sC)[q] = reinterpret_cast<const int32_t*>(cases + t.c)[q];
-    }
-    __syncthreads();
-    const CaseDev& C = sC;
-    const CaseView<Codec> V = case_view<Codec>(S, C);
-    const int j = t.j0 + threadIdx.x;
-    // 1. both nodes' own loads, issued before anything waits on memory
+    unsigned char* const base = const_cast<unsigned char*>(S.in) + (int64_t)g.blk0 * kB;  // the case's first block
+    auto node_at = [&](int kk, int jj) { return Node<Codec>{base + (int64_t)(kk * g.rowblk + (jj >> 5)) * kB, jj & 31}; };
+    const int j = g.j0 + threadIdx.x;
     F0T f0raw[2] = {};
     PT fraw[2][8], graw[2][9];
     Real chz_prev[2] = {}, chr_prev[2] = {}, p_prev[2] = {};
     bool in[2];
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
-        const int k = t.k0 + threadIdx.y + p * BZ;
-        in[p] = (j < C.nr) && (k < C.nz);
+        const int k = g.k0 + threadIdx.y + p * BZ;
+        in[p] = (j < g.nr) && (k < g.nz);
         if (in[p]) {
-            const Node<Codec> n = V.in_node(k * C.pitch + j);
+            const Node<Codec> n = node_at(k, j);
             f0raw[p] = n.f0();
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
@@ -692,26 +723,35 @@ step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
             graw[p][0] = n.g(0);
             chz_prev[p] = n.chz();
             chr_prev[p] = n.chr();
-            if (C.p_coupling == 1) p_prev[p] = n.p();
+        } else {
+            load_phi_raw<Codec>(node_at(ghost_z(k, g.nz, g.zper), ghost_r(j, g.nr)), f0raw[p], fraw[p]);
         }
     }
-    // 2. the ring of the phi window
-    for (int q = threadIdx.y * kTR + threadIdx.x; q < NRING; q += kTR * BZ) {
-        int a, b;
-        ring_cell<TZ>(q, a, b);
-        sphi[a * LD + b] = window_phi<Codec>(C, V, t, a, b, kG ? &T : nullptr);
+    // 2. the window: this thread's ring cell, then both nodes' own phi (Eq.
+    //    16, in the form of the one-node kernel), as soon as their loads land;
+    //    16-bit grid storage takes S_a of a column from grid_sa, the value the
+    //    column table holds
+    auto sa_of = [&](int jj) -> float {
+        if constexpr (kG) return grid_sa<Codec>(jj);
+        else return 0.0f;
+    };
+    if (q < NRING) {
+        int ra, rb;
+        ring_cell<TZ>(q, ra, rb);
+        const int rj = ghost_r(g.j0 - 2 + rb, g.nr);
+        F0T rf0;
+        PT rf[8];
+        load_phi_raw<Codec>(node_at(ghost_z(g.k0 - 2 + ra, g.nz, g.zper), rj), rf0, rf);
+        sphi[ra * LD + rb] = phi_of<Codec>(rf0, rf, rcp_((Real)rj + (Real)0.5), sa_of(rj));
     }
-    // 3. both nodes' own phi (Eq. 16), in the form of the one-node kernel
     const Real r = (Real)j + (Real)0.5;
     const int bo = threadIdx.x + 2;
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int a = threadIdx.y + 2 + p * BZ;
         if (in[p]) {
-            if constexpr (kG) {
-                sphi[a * LD + bo] = phi_of<Codec>(f0raw[p], fraw[p], rcp_(r), T.A[bo].w);
-            } else if constexpr (sizeof(PT) == 2) {
-                sphi[a * LD + bo] = phi_of<Codec>(f0raw[p], fraw[p], rcp_(r));
+            if constexpr (sizeof(PT) == 2) {
+                sphi[a * LD + bo] = phi_of<Codec>(f0raw[p], fraw[p], rcp_(r), sa_of(j));
             } else {
                 Real sum = (Real)f0_value(f0raw[p]);
 #pragma unroll
@@ -719,9 +759,15 @@ step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
                 sphi[a * LD + bo] = sum * rcp_(r);
             }
         } else {
-            sphi[a * LD + bo] = window_phi<Codec>(C, V, t, a, bo, kG ? &T : nullptr);
+            const int jm = ghost_r(j, g.nr);
+            sphi[a * LD + bo] = phi_of<Codec>(f0raw[p], fraw[p], rcp_((Real)jm + (Real)0.5), sa_of(jm));
         }
     }
+    // 3. the column table and the case record into shared memory
+    if constexpr (kG) {
+        if (q < LD) grid_tab_fill<Codec>(T, q, g.j0, g.nr);
+    }
+    if (q < kCW) reinterpret_cast<int32_t*>(&sC)[q] = cw;
     if constexpr (STASH) {
         // the second node's inputs to shared memory (one slot per thread)
         const int q = threadIdx.y * kTR + threadIdx.x;
@@ -737,14 +783,21 @@ step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
             st_g0[q] = graw[1][0];
             st_chz[q] = chz_prev[1];
             st_chr[q] = chr_prev[1];
-            st_p[q] = p_prev[1];
         }
     }
     __syncthreads();
+    const CaseDev& C = sC;
+    const CaseView<Codec> V = case_view<Codec>(S, C);
+    // the lagged pressure p^{n-1}, read only under the lagged coupling
+    if (C.p_coupling == 1) {
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+            if (in[p]) p_prev[p] = V.in_node((g.k0 + threadIdx.y + p * BZ) * C.pitch + j).p();
+    }
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         if (!in[p]) continue;
-        const int k = t.k0 + threadIdx.y + p * BZ;
+        const int k = g.k0 + threadIdx.y + p * BZ;
         if (STASH && p == 1) {
             // reloaded only now: the compiler may not hoist these shared loads
             // above the first node's update
@@ -760,7 +813,6 @@ step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
             graw[1][0] = st_g0[q];
             chz_prev[1] = st_chz[q];
             chr_prev[1] = st_chr[q];
-            p_prev[1] = st_p[q];
         }
         if constexpr (kG) {
             const TabCols cols{T, j == 0 ? bo : bo - 1, bo, j + 1 == C.nr ? bo : bo + 1};
@@ -779,10 +831,13 @@ step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
 // (the first inside the case; in1: the second too), from their raw stored
 // values and the row-pair phi window: decode and transform in node pairs, the
 // macroscopic step and both collisions in float2 lanes, then each node's
-// inverse transform and stores (step_kernel_pack2).  Measured: staging the
-// tiles of this update through shared memory with the TMA pipeline of
-// step_kernel_pipe (80 registers, 136 bytes of spill) took 1.16 ms on the
-// 512-case batch, against 0.657 ms here.
+// inverse transform and stores (step_kernel_pack2).  Measured on the
+// 512-case batch, against 0.657 ms in step_kernel_pack2 at the time: staging
+// the tiles of this update through shared memory with the TMA pipeline of
+// step_kernel_pipe (80 registers, 136 bytes of spill) took 1.16 ms; a
+// persistent kernel with one TMA stage refilled after the window barrier took
+// 0.721 ms at 2 CTAs per SM (128 registers) and 0.797 ms at 3 (160 bytes of
+// spill).
 template <class Codec, int RM, int LD>
 __device__ __forceinline__ void pack2_update(const CaseDev& C, const CaseView<Codec>& V, const float2* spair,
                                              const GridTab& T, int ty, int j, int k0,
@@ -850,52 +905,63 @@ __device__ __forceinline__ void pack2_update(const CaseDev& C, const CaseView<Co
 // spair[a][b] = (phi of window row a, of window row a + 8), so each stencil
 // point of both nodes is one 8-byte shared load.  Every lane computes exactly
 // what node_update_grid computes.
-// 3 CTAs per SM (80 registers, 68 bytes of spill): 0.674 ms on the 512-case
-// batch, against 0.805 ms at 2 (no spill) and 0.802 ms at 4.
+// The loads of the window phase are addressed from the tile's TileGeo record
+// alone and all leave before any of them is used: the case record (one word
+// per thread), both nodes' own values and the thread's ring cell.  The table
+// and the case record are stored while they are in flight, and one barrier
+// closes the window.  Measured on the 512-case batch: 0.600 ms, against
+// 0.658 ms when the case record was fetched and stored first (a barrier
+// before the own and ring loads) and 0.688 ms with the geometry record but
+// the case record fetched after the ring's loads were consumed.
+// 3 CTAs per SM (80 registers, 20 bytes of spill), against 0.805 ms at 2 (no
+// spill) and 0.802 ms at 4.
 #ifndef AXILBM_PACK2_CTAS
 #define AXILBM_PACK2_CTAS 3
 #endif
 
 template <class Codec, int RM>
 __global__ void __launch_bounds__(kTR * 8, AXILBM_PACK2_CTAS)
-step_kernel_pack2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ tiles, StateDev<Codec> S,
-                  const CUtensorMap* __restrict__ maps, int map_set, int parity, int ntiles, int ahead) {
+step_kernel_pack2(const CaseDev* __restrict__ cases, const TileGeo* __restrict__ geo, StateDev<Codec> S,
+                   const CUtensorMap* __restrict__ maps, int parity, int ntiles, int ahead) {
     static_assert(Codec::kGrid, "the FP16 grid codec's packed step");
     using PT = typename Codec::PT;
     using F0T = typename Codec::F0T;
     constexpr int BZ = 8, TZ = 2 * BZ, LD = kTR + 4, NP = BZ + 4;
     constexpr int NRING = 4 * kTR + 4 * (TZ + 4);
+    static_assert(NRING <= kTR * BZ, "one ring cell per thread at most");
+    constexpr int kB = Block<Codec>::bytes;
     __shared__ float2 spair[NP * LD];
     __shared__ __align__(16) CaseDev sC;
     __shared__ float4 sgA[LD], sgD[LD];
     __shared__ uint4 sgH[LD];
     const GridTab T{sgA, sgD, sgH};
-    const TileDev t = tiles[blockIdx.x];
+    const TileGeo g = geo[blockIdx.x];
     const int q = threadIdx.y * kTR + threadIdx.x;
-    if (q < LD) grid_tab_fill<Codec>(T, q, t.j0, cases[t.c].nr);
+    constexpr int kCW = (int)(sizeof(CaseDev) / 4);  // words of the case record
+    // 1. every load of the window phase is issued before any of them is used:
+    //    the case record word of this thread, both nodes' own values and the
+    //    raw values of this thread's ring cell
+    int32_t cw = 0;
+    if (q < kCW) cw = reinterpret_cast<const int32_t*>(cases + g.c)[q];
     if (maps != nullptr && q == 0 && (int)blockIdx.x + ahead < ntiles) {
-        const TileDev tp = tiles[blockIdx.x + ahead];
-        const CUtensorMap* M = maps + ((size_t)tp.c * 2 + map_set) * kMapsPerCase + 2 + parity;
+        // L2 prefetch of the tile one resident wave ahead
+        const TileGeo tp = geo[blockIdx.x + ahead];
+        const CUtensorMap* M = maps + ((size_t)tp.c * 2 + 1) * kMapsPerCase + 2 + parity;
         tensormap_acquire(M);
         tma_prefetch_4d(M, 0, 0, tp.j0 >> 5, tp.k0);
     }
-    if (q < (int)(sizeof(CaseDev) / 4))
-        reinterpret_cast<int32_t*>(&sC)[q] = reinterpret_cast<const int32_t*>(cases + t.c)[q];
-    __syncthreads();
-    const CaseDev& C = sC;
-    const CaseView<Codec> V = case_view<Codec>(S, C);
-    const int j = t.j0 + threadIdx.x;
-    // 1. both nodes' own loads
+    unsigned char* const base = const_cast<unsigned char*>(S.in) + (int64_t)g.blk0 * kB;  // the case's first block
+    const int j = g.j0 + threadIdx.x;
     F0T f0raw[2] = {};
     PT fraw[2][8], graw[2][9];
     float chz_prev[2] = {}, chr_prev[2] = {}, p_prev[2] = {};
     bool in[2];
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
-        const int k = t.k0 + threadIdx.y + p * BZ;
-        in[p] = (j < C.nr) && (k < C.nz);
+        const int k = g.k0 + threadIdx.y + p * BZ;
+        in[p] = (j < g.nr) && (k < g.nz);
         if (in[p]) {
-            const Node<Codec> n = V.in_node(k * C.pitch + j);
+            const Node<Codec> n{base + (int64_t)(k * g.rowblk + (j >> 5)) * kB, j & 31};
             f0raw[p] = n.f0();
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
@@ -906,32 +972,55 @@ step_kernel_pack2(const CaseDev* __restrict__ cases, const TileDev* __restrict__
             graw[p][0] = n.g(0);
             chz_prev[p] = n.chz();
             chr_prev[p] = n.chr();
-            if (C.p_coupling == 1) p_prev[p] = n.p();
         }
     }
-    // phi of window row a, column b into its row-pair slot(s)
+    int ra = 0, rb = 0, rj = 0;
+    F0T rf0 = {};
+    PT rf[8];
+    if (q < NRING) {
+        ring_cell<TZ>(q, ra, rb);
+        const int km = ghost_z(g.k0 - 2 + ra, g.nz, g.zper);
+        rj = ghost_r(g.j0 - 2 + rb, g.nr);
+        const Node<Codec> n{base + (int64_t)(km * g.rowblk + (rj >> 5)) * kB, rj & 31};
+        rf0 = n.f0();
+#pragma unroll
+        for (int i = 1; i < 9; ++i) rf[i - 1] = n.f(i);
+    }
+    // 2. the column table and the case record into shared memory
+    if (q < LD) grid_tab_fill<Codec>(T, q, g.j0, g.nr);
+    if (q < kCW) reinterpret_cast<int32_t*>(&sC)[q] = cw;
+    // 3. the window: the ring cell and both nodes' own phi
     auto put = [&](int a, int b, float v) {
         if (a < NP) spair[a * LD + b].x = v;
         if (a >= BZ) spair[(a - BZ) * LD + b].y = v;
     };
-    // 2. the ring of the phi window
-    for (int qq = q; qq < NRING; qq += kTR * BZ) {
-        int a, b;
-        ring_cell<TZ>(qq, a, b);
-        put(a, b, window_phi<Codec>(C, V, t, a, b, &T));
-    }
-    // 3. both nodes' own phi, in the form of the one-node kernel
+    if (q < NRING) put(ra, rb, phi_of<Codec>(rf0, rf, rcp_((float)rj + 0.5f), grid_sa<Codec>(rj)));
     const float r = (float)j + 0.5f;
     const int bo = threadIdx.x + 2;
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int a = threadIdx.y + 2 + p * BZ;
-        put(a, bo, in[p] ? phi_of<Codec>(f0raw[p], fraw[p], rcp_(r), T.A[bo].w)
-                         : window_phi<Codec>(C, V, t, a, bo, &T));
+        if (in[p]) {
+            put(a, bo, phi_of<Codec>(f0raw[p], fraw[p], rcp_(r), grid_sa<Codec>(j)));
+        } else {
+            const int km = ghost_z(g.k0 + threadIdx.y + p * BZ, g.nz, g.zper);
+            const int jm = ghost_r(j, g.nr);
+            const Node<Codec> n{base + (int64_t)(km * g.rowblk + (jm >> 5)) * kB, jm & 31};
+            put(a, bo, node_phi<Codec>(n, rcp_((float)jm + 0.5f), grid_sa<Codec>(jm)));
+        }
     }
     __syncthreads();
     if (!in[0]) return;  // the second node lies below the first
-    pack2_update<Codec, RM, LD>(C, V, spair, T, threadIdx.y, j, t.k0 + threadIdx.y, f0raw, fraw, graw, chz_prev,
+    const CaseDev& C = sC;
+    const CaseView<Codec> V = case_view<Codec>(S, C);
+    // the lagged pressure p^{n-1}, read only under the lagged coupling (a flag
+    // of the case record)
+    if (C.p_coupling == 1) {
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+            if (in[p]) p_prev[p] = V.in_node((g.k0 + threadIdx.y + p * BZ) * C.pitch + j).p();
+    }
+    pack2_update<Codec, RM, LD>(C, V, spair, T, threadIdx.y, j, g.k0 + threadIdx.y, f0raw, fraw, graw, chz_prev,
                                 chr_prev, p_prev, in[1]);
 }
 
@@ -1451,7 +1540,8 @@ void launch_step_rates(int variant, int ntiles, cudaStream_t st, const CaseDev* 
         case 7:
             if constexpr (Codec::kGrid)
                 step_kernel_pack2<Codec, RM><<<ntiles, dim3(kTR, 8), 0, st>>>(
-                    cs, tiles, S, maps, 1, parity, ntiles, kPrefetchQuarters * sms * AXILBM_PACK2_CTAS / 4);
+                    cs, reinterpret_cast<const TileGeo*>(tiles + ntiles), S, maps, parity, ntiles,
+                    kPrefetchQuarters * sms * AXILBM_PACK2_CTAS / 4);
             else if constexpr (sizeof(typename Codec::Real) == 4)
                 step_kernel_seq2<Codec, 8, RM><<<ntiles, dim3(kTR, 8), 0, st>>>(
                     cs, tiles, S, maps, 1, parity, ntiles, kPrefetchQuarters * sms * seq2_min_blocks<Codec, 8, RM>() / 4);
