@@ -290,7 +290,8 @@ struct CodecGrid16 {
     __device__ static float grid_h(float f, const GridCol& g, bool D) {
         return __fadd_rn(__fmaf_rn(f, D ? g.invS_d : g.invS_a, kMagic - 0.5f), -kMagic);
     }
-    // f and g of a direction as one stored pair
+    // f and g of a direction as one stored pair (a packed FMA and add for
+    // both, bit-identical, measured 1.5 % slower in the packed two-node step)
     __device__ static PT2 enc_pair(float f, float gv, const GridCol& g, bool D) {
         PT2 e;
         e.x = to16<PT>(grid_h(f, g, D));
@@ -928,7 +929,9 @@ __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, 
         const Real qb = (Real)1 - A1 * cb + (Real)2 * A2 * ca * cb;
         const Real qc = -(A0 + A1 * ca - A2 * ca * ca);
         const Real disc = qb * qb - (Real)4 * qa * qc;
-        m.p = (disc >= (Real)0) ? div_((Real)-2 * qc, qb + sqrt_(disc)) : div_(-qc, qb);
+        // one division: the root's numerator and denominator are selected first
+        const bool two = disc >= (Real)0;
+        m.p = div_(two ? (Real)-2 * qc : -qc, two ? qb + sqrt_(disc) : qb);
         m.pstar = m.p;
         m.ur = ca + cb * m.p;
     }

@@ -273,6 +273,9 @@ __device__ __forceinline__ void node_macros(const CaseDev& C, const V* sphi, int
         const V qb = vfma(vmul(bc<V>((S)2), A2cb), ca, vfma(vneg(A1), cb, bc<V>((S)1)));
         const V qc = vneg(vfma(vneg(vmul(A2, ca)), ca, vfma(A1, ca, A0)));
         const V disc = vfma(qb, qb, vmul(vmul(bc<V>((S)-4), qa), qc));
+        // both roots' divisions, then the select (selecting the numerator and
+        // denominator first is bit-identical and measured 2 % slower in the
+        // packed two-node step)
         m.p = sel_ge0(disc, div_(vmul(bc<V>((S)-2), qc), vadd(qb, sqrt_(disc))), div_(vneg(qc), qb));
         m.pstar = m.p;
         m.ur = vfma(cb, m.p, ca);
