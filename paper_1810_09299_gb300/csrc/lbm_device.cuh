@@ -557,15 +557,26 @@ __device__ __forceinline__ typename Codec::Real node_phi(const Node<Codec>& n, t
 }
 // ---------------------------------------------------------------- arithmetic helpers
 // FP32: the hardware approximate reciprocal, division and square root (a few
-// ulp, far below the FP32 rounding the method accumulates over a run);
+// ulp, far below the FP32 rounding the method accumulates over a run), with
+// subnormal inputs and results flushed to zero (PTX .approx.ftz): values
+// below 2^-126 arise only in the far field at rest, and the forms that keep
+// them cost 1.7 % (FP32) to 3.5 % (16-bit storage) of the step;
 // FP64: IEEE division and square root, as in the oracle.
-__device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float rcp_(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
-__device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float div_(float a, float b) {
+    float y;
+    asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(y) : "f"(a), "f"(b));
+    return y;
+}
 __device__ __forceinline__ double div_(double a, double b) { return a / b; }
 __device__ __forceinline__ float sqrt_(float x) {
     float y;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
