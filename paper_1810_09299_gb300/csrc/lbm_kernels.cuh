@@ -121,7 +121,8 @@ __device__ __forceinline__ void ring_cell(int q, int& a, int& b) {
 // FP16 and -5.1 % in BF16 storage with the paper's collision, with the same
 // results.  The raw-moment collision in bfloat16 storage spills more at 48
 // registers and keeps 4 CTAs (0.772 against 0.817 ms); with FP16's grid
-// codec it takes 5 (0.778 against 0.802 ms).  General rates: 4 CTAs
+// codec it took 5 (0.778 against 0.802 ms) until the loads-first window
+// phase (see below).  General rates: 4 CTAs
 // of 8 rows (64 registers, a few bytes of spill): on the 512-case batch with
 // every rate equal, -10.6 % in FP32 and -8.6 % in FP16 storage against 3 CTAs
 // at 80 registers.  AXILBM_GENERAL_CTAS overrides the count when building for
@@ -129,18 +130,22 @@ __device__ __forceinline__ void ring_cell(int q, int& a, int& b) {
 #ifndef AXILBM_GENERAL_CTAS
 #define AXILBM_GENERAL_CTAS 4
 #endif
-// AXILBM_STEP16_CTAS, AXILBM_RAW16_CTAS: the same counts for the 16-bit
-// kernels (the raw-moment one with FP16's grid codec), for tuning builds.
+// With the loads-first window phase the one-node FP16 kernels spill at 48
+// registers: 4 CTAs measured 0.763 against 0.792 ms (paper's collision) and
+// 0.798 against 0.874 ms (raw moments), while bfloat16 keeps 5 (0.734 against
+// 0.776 ms).  AXILBM_STEP16_CTAS (bfloat16) and AXILBM_GRID16_CTAS (FP16's
+// grid codec, both collisions) override the counts for tuning builds.
 #ifndef AXILBM_STEP16_CTAS
 #define AXILBM_STEP16_CTAS 5
 #endif
-#ifndef AXILBM_RAW16_CTAS
-#define AXILBM_RAW16_CTAS 5
+#ifndef AXILBM_GRID16_CTAS
+#define AXILBM_GRID16_CTAS 4
 #endif
 template <class Codec, int BZ, int RM>
 constexpr int step_min_blocks() {
-    constexpr int bz8 = (RM == kRatesPaperRaw && sizeof(typename Codec::PT) == 2)
-                            ? (Codec::kGrid ? AXILBM_RAW16_CTAS : 4)
+    constexpr int bz8 = Codec::kGrid ? AXILBM_GRID16_CTAS
+                        : (RM == kRatesPaperRaw && sizeof(typename Codec::PT) == 2)
+                            ? 4
                             : (sizeof(typename Codec::PT) == 2 ? AXILBM_STEP16_CTAS : 5);
     return sizeof(typename Codec::Real) == 8 ? 1
            : RM != kRatesGeneral ? (BZ >= 16 ? 2 : (BZ >= 8 ? bz8 : 8))
