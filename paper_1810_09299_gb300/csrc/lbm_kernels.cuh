@@ -833,43 +833,47 @@ step_kernel_seq2(const CaseDev* __restrict__ cases, const TileDev* __restrict__ 
 }
 
 // The packed update of the two nodes (k0, j) and (k0 + 8, j) of one thread
-// (the first inside the case; in1: the second too), from their raw stored
-// values and the row-pair phi window: decode and transform in node pairs, the
-// macroscopic step and both collisions in float2 lanes, then each node's
-// inverse transform and stores (step_kernel_pack2).  Measured on the
-// 512-case batch, against 0.657 ms in step_kernel_pack2 at the time: staging
-// the tiles of this update through shared memory with the TMA pipeline of
-// step_kernel_pipe (80 registers, 136 bytes of spill) took 1.16 ms; a
-// persistent kernel with one TMA stage refilled after the window barrier took
-// 0.721 ms at 2 CTAs per SM (128 registers) and 0.797 ms at 3 (160 bytes of
-// spill).
-template <class Codec, int RM, int LD>
-__device__ __forceinline__ void pack2_update(const CaseDev& C, const CaseView<Codec>& V, const float2* spair,
-                                             const GridTab& T, int ty, int j, int k0,
-                                             const typename Codec::F0T* f0raw, const typename Codec::PT (*fraw)[8],
-                                             const typename Codec::PT (*graw)[9], const float* chz_prev,
-                                             const float* chr_prev, const float* p_prev, bool in1) {
-    constexpr int BZ = 8;
-    const int bo = (j & 31) + 2;  // the window column of j (tiles start at multiples of 32)
-    const TabCols cols{T, j == 0 ? bo : bo - 1, bo, j + 1 == C.nr ? bo : bo + 1};
-    // 4. decode both nodes and transform them in node pairs: M f and M g of
-    //    (node 0, node 1) by the packed transforms of the one-node kernels
-    //    (there they pair (f_i, g_i) of one node; each lane takes the same
-    //    operations either way).  Against decoding each node with node_pre
-    //    and repacking: fewer moves and spills, 0.670 against 0.674 ms
-    const GridCol go = cols.get(1);
-    float2 x[9], mf[9], mg[9];
+// of step_kernel_pack2, in two parts: pack2_moments decodes both nodes and
+// transforms them in node pairs; pack2_finish runs the macroscopic step and
+// both collisions in float2 lanes, then each node's inverse transform and
+// stores.  Measured on the 512-case batch, against 0.657 ms in
+// step_kernel_pack2 at the time: staging the tiles of this update through
+// shared memory with the TMA pipeline of step_kernel_pipe (80 registers, 136
+// bytes of spill) took 1.16 ms; a persistent kernel with one TMA stage
+// refilled after the window barrier took 0.721 ms at 2 CTAs per SM (128
+// registers) and 0.797 ms at 3 (160 bytes of spill).
+//
+// Step 4: M f and M g of (node 0, node 1) by the packed transforms of the
+// one-node kernels (there they pair (f_i, g_i) of one node; each lane takes
+// the same operations either way).  go: the constants of the nodes' column.
+template <class Codec>
+__device__ __forceinline__ void pack2_moments(const GridCol& go, const typename Codec::F0T* f0raw,
+                                              const typename Codec::PT (*fraw)[8], const typename Codec::PT (*graw)[9],
+                                              float2* mf, float2* mg, float2& g0) {
+    float2 x[9];
     x[0] = make_float2(f0raw[0], f0raw[1]);
 #pragma unroll
     for (int i = 1; i < 9; ++i)
         x[i] = make_float2(Codec::dec_f(fraw[0][i - 1], go, i > 4), Codec::dec_f(fraw[1][i - 1], go, i > 4));
     moments_p(x, mf);
     x[0] = make_float2(Codec::dec_g0(graw[0][0], go), Codec::dec_g0(graw[1][0], go));
-    const float2 g0 = x[0];
+    g0 = x[0];
 #pragma unroll
     for (int i = 1; i < 9; ++i)
         x[i] = make_float2(Codec::dec_g(graw[0][i], go, i > 4), Codec::dec_g(graw[1][i], go, i > 4));
     moments_p(x, mg);
+}
+
+// Steps 5 and 6, from the moments of both nodes (the first node inside the
+// case; in1: the second too) and the row-pair phi window.
+template <class Codec, int RM, int LD>
+__device__ __forceinline__ void pack2_finish(const CaseDev& C, const CaseView<Codec>& V, const float2* spair,
+                                             const GridTab& T, int ty, int j, int k0, const float2* mf,
+                                             const float2* mg, float2 g0, const float* chz_prev,
+                                             const float* chr_prev, const float* p_prev, bool in1) {
+    constexpr int BZ = 8;
+    const int bo = (j & 31) + 2;  // the window column of j (tiles start at multiples of 32)
+    const TabCols cols{T, j == 0 ? bo : bo - 1, bo, j + 1 == C.nr ? bo : bo + 1};
     // 5. the macroscopic step and both collisions once for both nodes
     lane::Macro<float2> m;
     lane::node_macros<float2, LD, RM, true>(C, spair, ty + 2, bo, j, mg, g0,
@@ -1014,6 +1018,12 @@ step_kernel_pack2(const CaseDev* __restrict__ cases, const TileGeo* __restrict__
             put(a, bo, node_phi<Codec>(n, rcp_((float)jm + 0.5f), grid_sa<Codec>(jm)));
         }
     }
+    // 4. both nodes' moments while other warps still wait for their loads
+    //    (the column's constants computed, as the table holds them).
+    //    Measured against forming them after the barrier: 0.572 against
+    //    0.580 ms, and 0.598 against 0.646 ms with raw moments
+    float2 mf[9], mg[9], g0;
+    pack2_moments<Codec>(grid_col<Codec>(j), f0raw, fraw, graw, mf, mg, g0);
     __syncthreads();
     if (!in[0]) return;  // the second node lies below the first
     const CaseDev& C = sC;
@@ -1025,8 +1035,8 @@ step_kernel_pack2(const CaseDev* __restrict__ cases, const TileGeo* __restrict__
         for (int p = 0; p < 2; ++p)
             if (in[p]) p_prev[p] = V.in_node((g.k0 + threadIdx.y + p * BZ) * C.pitch + j).p();
     }
-    pack2_update<Codec, RM, LD>(C, V, spair, T, threadIdx.y, j, g.k0 + threadIdx.y, f0raw, fraw, graw, chz_prev,
-                                chr_prev, p_prev, in[1]);
+    pack2_finish<Codec, RM, LD>(C, V, spair, T, threadIdx.y, j, g.k0 + threadIdx.y, mf, mg, g0, chz_prev, chr_prev,
+                                p_prev, in[1]);
 }
 
 // Shared-memory layout of one stage of the TMA-pipelined step for tile
