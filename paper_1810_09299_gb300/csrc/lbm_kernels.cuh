@@ -944,12 +944,14 @@ __device__ __forceinline__ void pack2_finish(const CaseDev& C, const CaseView<Co
 // alone and all leave before any of them is used: the case record (one word
 // per thread), both nodes' own values and the thread's ring cell.  The table
 // and the case record are stored while they are in flight, and one barrier
-// closes the window.  Measured on the 512-case batch: 0.600 ms, against
-// 0.658 ms when the case record was fetched and stored first (a barrier
-// before the own and ring loads) and 0.688 ms with the geometry record but
-// the case record fetched after the ring's loads were consumed.
-// 3 CTAs per SM (80 registers, 20 bytes of spill), against 0.805 ms at 2 (no
-// spill) and 0.802 ms at 4.
+// closes the window; both nodes' moments are formed before it.  Measured on
+// the 512-case batch, before the moments moved ahead of the barrier and the
+// FP32 approximations flushed subnormals (0.572 ms with both): 0.600 ms,
+// against 0.658 ms when the case record was fetched and stored first (a
+// barrier before the own and ring loads) and 0.688 ms with the geometry
+// record but the case record fetched after the ring's loads were consumed.
+// 3 CTAs per SM (80 registers, 20 bytes of spill); on the current build 2
+// CTAs (no spill) take 0.664 ms and 4 take 0.596 ms.
 #ifndef AXILBM_PACK2_CTAS
 #define AXILBM_PACK2_CTAS 3
 #endif
@@ -957,7 +959,7 @@ __device__ __forceinline__ void pack2_finish(const CaseDev& C, const CaseView<Co
 template <class Codec, int RM>
 __global__ void __launch_bounds__(kTR * 8, AXILBM_PACK2_CTAS)
 step_kernel_pack2(const CaseDev* __restrict__ cases, const TileGeo* __restrict__ geo, StateDev<Codec> S,
-                   const CUtensorMap* __restrict__ maps, int parity, int ntiles, int ahead) {
+                  const CUtensorMap* __restrict__ maps, int parity, int ntiles, int ahead) {
     static_assert(Codec::kGrid, "the FP16 grid codec's packed step");
     using PT = typename Codec::PT;
     using F0T = typename Codec::F0T;
