@@ -75,22 +75,12 @@ __device__ __forceinline__ typename Codec::Real node_phi_at(const CaseView<Codec
     return node_phi<Codec>(V.in_node(loc), rcp_(r), Sa);
 }
 
-// phi at window position (a, b) of tile t through the ghost rules; T: the
-// tile's GridTab when there is one (16-bit storage), else P and c of the
-// column are computed.
+// phi at window position (a, b) of tile t through the ghost rules.
 template <class Codec>
 __device__ __forceinline__ typename Codec::Real window_phi(const CaseDev& C, const CaseView<Codec>& V,
-                                                            const TileDev& t, int a, int b,
-                                                            const GridTab* T = nullptr) {
-    using Real = typename Codec::Real;
+                                                            const TileDev& t, int a, int b) {
     const int k = ghost_z(t.k0 - 2 + a, C.nz, C.zper);
     const int j = ghost_r(t.j0 - 2 + b, C.nr);
-    if constexpr (Codec::kGrid) {
-        if (T != nullptr) {
-            const Real r = (Real)j + (Real)0.5;
-            return node_phi<Codec>(V.in_node(k * C.pitch + j), rcp_(r), T->A[b].w);
-        }
-    }
     return node_phi_at<Codec>(V, k * C.pitch + j, j);
 }
 
