@@ -873,14 +873,22 @@ __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, 
     // interface moves or stays), so the FP32 forms keep their tested numbers.
     constexpr bool kMergeRcp = sizeof(Real) == 8;
     const Real rt = m.rho * (m.r + m.nu * m.inv_r);
-    Real sgv, iDr;
+    // the interface normal's denominator |grad phi| + n_eps (Eq. 2)
+    const Real nden = sqrt_(m.gz * m.gz + m.gr * m.gr) + (VP ? (Real)v1.y : P.n_eps);
+    Real sgv, iDr, ign;
     if constexpr (kMergeRcp) {
-        const Real X = rcp_(rt * tau_g);
+        // one division for 1 / tau_g, 1 / (r rho + nu rho / r) and the
+        // normal's 1 / nden: Y = 1 / (rho (r + nu / r) tau_g nden)
+        const Real rtt = rt * tau_g;
+        const Real Y = rcp_(rtt * nden);
+        const Real X = Y * nden;
         sgv = X * rt;
         iDr = X * tau_g;
+        ign = Y * rtt;
     } else {
         sgv = rcp_(tau_g);
         iDr = rcp_(m.r * m.rho + m.nu * m.rho * m.inv_r);
+        ign = rcp_(nden);
     }
     if constexpr (RM == kRatesPaper) {
         m.sg[1] = sgv;
@@ -897,7 +905,6 @@ __device__ __forceinline__ void node_macros(const CaseDev& C, const Real* sphi, 
     const Real Fsz = mut * m.gz, Fsr = mut * m.gr;
     const Real Gz = (m.rho - rho_l) * (VP ? (Real)v1.x : P.grav_z);
     // interface normal and lambda (Eq. 2)
-    const Real ign = rcp_(sqrt_(m.gz * m.gz + m.gr * m.gr) + (VP ? (Real)v1.y : P.n_eps));
     m.nzn = m.gz * ign;
     m.nrn = m.gr * ign;
     m.lam = (Real)4 * m.phi * ((Real)1 - m.phi) * P.inv_W;
