@@ -65,7 +65,7 @@ TRAFFIC_B_PER_NODE = {("fp32", 5, "orthogonal"): 163.96}
 # (profiles/step_kernel_fp64_batched64cases.md), against the pipe's rate
 # measured in the same run (lbm_measure_fp64_rate: dependent FP64 FMA chains
 # timed with CUDA events).
-FP64_OPS_PER_NODE = 385.5
+FP64_OPS_PER_NODE = 383.3
 # What the GPU parity tests hold each precision to against the FP64 oracle.
 PARITY_TOL = {
     "fp64": "phi, rho, u, p within 1e-11 (relative max-norm) of the FP64 oracle",
