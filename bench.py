@@ -59,7 +59,7 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "mix_fp16": "f32 (fp16 storage)", "mix_bf
 # autotuner picks for FP32, re-captured on the current build).  Scaled to a
 # full launch by the node count.  Kept only for the kernel builds captured
 # (another variant reports null).
-TRAFFIC_B_PER_NODE = {("fp32", 5, "orthogonal"): 163.96}
+TRAFFIC_B_PER_NODE = {("fp32", 5, "orthogonal"): 163.88}
 # The FP64 step is bound by the FP64 pipe, not by HBM: FP64-pipe thread
 # instructions (DADD + DFMA + DMUL) per node update from one ncu capture
 # (profiles/step_kernel_fp64_batched64cases.md), against the pipe's rate
