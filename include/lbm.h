@@ -48,7 +48,10 @@ typedef enum {
 
 /* Storage and arithmetic precision of a handle.
  *   LBM_FP64      populations and arithmetic in FP64.
- *   LBM_FP32      populations f_1..8 and g_0..8 in FP32, arithmetic in FP32.
+ *   LBM_FP32      populations f_1..8 and g_0..8 in FP32, arithmetic in FP32
+ *                 (reciprocals, divisions and square roots by the hardware
+ *                 approximations, a few ulp, subnormal operands and results
+ *                 flushed to zero; the same in the two 16-bit forms).
  *                 f_0 is stored as a pair of FP32 numbers holding the node's
  *                 mass ledger: (sum of its incoming populations) minus (its
  *                 stored outgoing f_1..8), accumulated with error-free FP32
